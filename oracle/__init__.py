@@ -1,0 +1,234 @@
+"""Vecchia log-likelihood ORACLE — test infrastructure, not part of the product.
+
+A plain, slow FP64 CPU implementation of the Vecchia-approximated Gaussian
+log-likelihood (arXiv 2403.07412), written from the paper and sharing no code
+with the CUDA library.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import it.
+
+What each function follows:
+
+* :func:`matern` — Eq. (2) (Sec. IV-A), through ``std::cyl_bessel_k``.
+* :func:`loglik_exact` — Eq. (1), dense, with the oracle's own Cholesky.
+* :func:`order_random` / :func:`order_maxmin` — Sec. V-A orderings
+  (random = splitmix64-driven Fisher–Yates; maxmin = greedy farthest point
+  from the point nearest the centroid, ties to the lowest index).
+* :func:`knn_rows` — Algorithm 1, nearest-neighbour loop: the m nearest
+  *previously ordered* points, ties by index, brute force.
+* :func:`vecchia_rows` / :func:`vecchia` — Sec. V-B: the Vecchia product of
+  univariate conditionals, explicit conditional mean and variance, and the
+  gradient in (sigma^2, beta, tau^2) by the joint-minus-marginal trace identity.
+
+Every function here is pinned by ``tests/test_oracle_pins.py``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "vecchia_oracle.cpp")
+_LIB = os.path.join(_HERE, "_liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_u64p = ctypes.POINTER(ctypes.c_uint64)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle's C++ source into ``oracle/_liboracle.so``."""
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    cmd = ["g++", "-O2", "-std=c++17", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared",
+           _SRC, "-o", tmp]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = ctypes.CDLL(build())
+        c_int, c_i64, c_i32, c_d, c_u64 = (ctypes.c_int, ctypes.c_int64, ctypes.c_int32,
+                                            ctypes.c_double, ctypes.c_uint64)
+        sig = {
+            "oracle_num_threads": (c_int, []),
+            "oracle_set_threads": (None, [c_int]),
+            "oracle_matern": (c_int, [c_i64, _dp, c_d, c_d, c_d, _dp]),
+            "oracle_matern_dbeta": (c_int, [c_i64, _dp, c_d, c_d, c_d, _dp]),
+            "oracle_bessel_k": (c_int, [c_i64, _dp, c_d, _dp]),
+            "oracle_splitmix64": (None, [c_u64, c_i64, _u64p]),
+            "oracle_order_random": (c_int, [c_i64, c_u64, _i64p]),
+            "oracle_order_maxmin": (c_int, [c_i64, _dp, _i64p]),
+            "oracle_knn_rows": (c_int, [c_i64, _dp, c_i32, _i64p, c_i64, _i32p]),
+            "oracle_vecchia_rows": (c_int, [c_i64, _dp, _dp, c_i32, _dp, _i64p, c_i64, _i32p, c_int,
+                                            _dp, _dp, _i64p]),
+            "oracle_sum_columns": (None, [c_i64, c_i32, _dp, _dp]),
+            "oracle_loglik_exact": (c_int, [c_i64, _dp, _dp, _dp, _dp, _dp]),
+            "oracle_block_logdensity": (c_int, [c_i32, _dp, _dp, _dp]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _p(a, t):
+    return a.ctypes.data_as(t)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def set_threads(t: int) -> None:
+    _load().oracle_set_threads(int(t))
+
+
+def num_threads() -> int:
+    return int(_load().oracle_num_threads())
+
+
+def matern(d, sigma2: float, beta: float, nu: float) -> np.ndarray:
+    """Eq. (2) covariance at distances ``d`` (C(0) = sigma2)."""
+    d = _f64(np.atleast_1d(d))
+    out = np.empty_like(d)
+    _load().oracle_matern(d.size, _p(d, _dp), sigma2, beta, nu, _p(out, _dp))
+    return out
+
+
+def matern_dbeta(d, sigma2: float, beta: float, nu: float) -> np.ndarray:
+    """dC/dbeta of Eq. (2) at distances ``d``."""
+    d = _f64(np.atleast_1d(d))
+    out = np.empty_like(d)
+    _load().oracle_matern_dbeta(d.size, _p(d, _dp), sigma2, beta, nu, _p(out, _dp))
+    return out
+
+
+def bessel_k(x, nu: float) -> np.ndarray:
+    """K_nu(x) as the oracle evaluates it (``std::cyl_bessel_k``)."""
+    x = _f64(np.atleast_1d(x))
+    out = np.empty_like(x)
+    _load().oracle_bessel_k(x.size, _p(x, _dp), nu, _p(out, _dp))
+    return out
+
+
+def splitmix64(seed: int, count: int) -> np.ndarray:
+    out = np.empty(count, dtype=np.uint64)
+    _load().oracle_splitmix64(ctypes.c_uint64(seed), count, _p(out, _u64p))
+    return out
+
+
+def order_random(n: int, seed: int) -> np.ndarray:
+    """Random ordering: perm[k] = original index of the k-th ordered location."""
+    perm = np.empty(n, dtype=np.int64)
+    _load().oracle_order_random(n, ctypes.c_uint64(seed), _p(perm, _i64p))
+    return perm
+
+
+def order_maxmin(xy) -> np.ndarray:
+    """Exact maxmin ordering, O(n^2)."""
+    xy = _f64(xy).reshape(-1, 2)
+    perm = np.empty(xy.shape[0], dtype=np.int64)
+    _load().oracle_order_maxmin(xy.shape[0], _p(xy, _dp), _p(perm, _i64p))
+    return perm
+
+
+def knn_rows(xy_ordered, m: int, rows=None) -> np.ndarray:
+    """Conditioning sets (ordered indices, -1 padded) of the given ordered rows."""
+    xy = _f64(xy_ordered).reshape(-1, 2)
+    n = xy.shape[0]
+    rows = np.arange(n, dtype=np.int64) if rows is None else np.ascontiguousarray(rows, dtype=np.int64)
+    out = np.empty((rows.size, m), dtype=np.int32)
+    rc = _load().oracle_knn_rows(n, _p(xy, _dp), m, _p(rows, _i64p), rows.size, _p(out, _i32p))
+    if rc:
+        raise ValueError("oracle_knn_rows: invalid arguments")
+    return out
+
+
+class OracleNotPD(RuntimeError):
+    def __init__(self, row):
+        super().__init__(f"conditional block not positive definite at ordered location {row}")
+        self.row = row
+
+
+def vecchia_rows(xy_ordered, y_ordered, m: int, theta, rows=None, nbr=None, want_grad=False,
+                 return_mu_s=False):
+    """Per-location Vecchia terms (and gradients) for the given ordered rows.
+
+    theta = (sigma2, beta, nu, tau2).  Returns an array of shape (nrows,) or
+    (nrows, 4) = (l_i, dl_i/dsigma2, dl_i/dbeta, dl_i/dtau2).
+    """
+    xy = _f64(xy_ordered).reshape(-1, 2)
+    y = _f64(y_ordered)
+    n = xy.shape[0]
+    rows = np.arange(n, dtype=np.int64) if rows is None else np.ascontiguousarray(rows, dtype=np.int64)
+    if nbr is None:
+        nbr = knn_rows(xy, m, rows)
+    nbr = np.ascontiguousarray(nbr, dtype=np.int32)
+    th = _f64(theta)
+    w = 4 if want_grad else 1
+    out = np.empty((rows.size, w), dtype=np.float64)
+    mu_s = np.empty((rows.size, 2), dtype=np.float64)
+    bad = np.full(1, -1, dtype=np.int64)
+    rc = _load().oracle_vecchia_rows(n, _p(xy, _dp), _p(y, _dp), m, _p(th, _dp), _p(rows, _i64p),
+                                     rows.size, _p(nbr, _i32p), 1 if want_grad else 0, _p(out, _dp),
+                                     _p(mu_s, _dp), _p(bad, _i64p))
+    if rc:
+        raise OracleNotPD(int(bad[0]))
+    res = out if want_grad else out[:, 0]
+    return (res, mu_s) if return_mu_s else res
+
+
+def compensated_sum(v) -> np.ndarray:
+    """Neumaier-compensated column sums in row order."""
+    v = _f64(v)
+    if v.ndim == 1:
+        v = v[:, None]
+    out = np.empty(v.shape[1], dtype=np.float64)
+    _load().oracle_sum_columns(v.shape[0], v.shape[1], _p(v, _dp), _p(out, _dp))
+    return out
+
+
+def vecchia(xy_ordered, y_ordered, m: int, theta, want_grad=False):
+    """Vecchia log-likelihood over all ordered locations: l or (l, dsigma2, dbeta, dtau2)."""
+    terms = vecchia_rows(xy_ordered, y_ordered, m, theta, want_grad=want_grad)
+    s = compensated_sum(terms)
+    return s if want_grad else float(s[0])
+
+
+def loglik_exact(xy, y, theta, want_grad=False):
+    """Eq. (1): exact zero-mean Gaussian log-likelihood (dense, O(n^3))."""
+    xy = _f64(xy).reshape(-1, 2)
+    y = _f64(y)
+    th = _f64(theta)
+    out = np.empty(1)
+    g = np.empty(3)
+    rc = _load().oracle_loglik_exact(xy.shape[0], _p(xy, _dp), _p(y, _dp), _p(th, _dp), _p(out, _dp),
+                                     _p(g, _dp) if want_grad else None)
+    if rc:
+        raise OracleNotPD(-1)
+    return (float(out[0]), g) if want_grad else float(out[0])
+
+
+def block_logdensity(S, y) -> float:
+    """log N(y; 0, S) of one dense block."""
+    S = _f64(S)
+    y = _f64(y)
+    out = np.empty(1)
+    rc = _load().oracle_block_logdensity(y.size, _p(S, _dp), _p(y, _dp), _p(out, _dp))
+    if rc:
+        raise OracleNotPD(-1)
+    return float(out[0])
