@@ -1,0 +1,164 @@
+/*
+ * vecchia.h — C ABI of the GB300-native Vecchia log-likelihood library (libvecchia.so).
+ *
+ * The library evaluates the Vecchia approximation of the zero-mean Gaussian-process
+ * log-likelihood of arXiv 2403.07412 (Sec. V-B, Algorithm 1) with the Matérn
+ * covariance of Eq. (2) plus a nugget:
+ *
+ *   l(theta) = sum_i log N(y_i | mu_i, s_i),
+ *   mu_i = Sigma_iJ Sigma_JJ^{-1} y_J,  s_i = Sigma_ii - Sigma_iJ Sigma_JJ^{-1} Sigma_Ji,
+ *   Sigma_pq = C(||s_p - s_q||) + tau2 [p == q],
+ *   C(d) = sigma2 2^{1-nu}/Gamma(nu) (d/beta)^nu K_nu(d/beta),  C(0) = sigma2,
+ *
+ * where J = J_i holds the m_i = min(i, m) nearest previously ordered locations of the
+ * i-th ordered location (0-based i).  theta is passed as double[4] =
+ * {sigma2, beta, nu, tau2}.
+ *
+ * Conventions for every entry point:
+ *   - Return value: a VECCHIA_* status code; nothing aborts or prints.
+ *   - "_dev" pointers are CUDA device pointers on the current device; "_host" and
+ *     unsuffixed array pointers are host memory.  The caller owns every buffer it
+ *     passes; the library never keeps a caller pointer after a call returns.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Calls that take a stream only enqueue work on it and return before the GPU
+ *     finishes; results are valid once that stream has been synchronised.
+ *   - A plan may be used by one stream at a time: calls that share a plan must be
+ *     ordered on the same stream (or externally synchronised).
+ *   - Failures found on the GPU (a conditional block that is not positive
+ *     definite) cannot be returned by the asynchronous call itself: the affected
+ *     outputs become NaN and vecchia_last_error_location() reports the first
+ *     failing ordered location.
+ */
+#ifndef VECCHIA_H
+#define VECCHIA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct vecchia_plan* vecchia_plan_t; /* opaque; immutable after create */
+
+enum {
+  VECCHIA_OK = 0,
+  VECCHIA_EINVAL = 1,   /* an argument is out of range or not finite            */
+  VECCHIA_ENOTPD = 2,   /* a conditional block was not positive definite        */
+  VECCHIA_ECUDA = 3,    /* a CUDA runtime call failed                           */
+  VECCHIA_ETIMEOUT = 4, /* a bounded device-side wait expired                   */
+  VECCHIA_ENOMEM = 5    /* device or host allocation failed                     */
+};
+
+enum {
+  VECCHIA_ORDER_GIVEN = 0,  /* use perm_in                                          */
+  VECCHIA_ORDER_RANDOM = 1, /* Sec. V-A random ordering (splitmix64 Fisher–Yates)   */
+  VECCHIA_ORDER_MAXMIN = 2  /* Sec. V-A maxmin ordering (exact greedy farthest point) */
+};
+
+/* Largest conditioning-set size m accepted by the likelihood kernels. */
+#define VECCHIA_MAX_M 63
+
+/*
+ * vecchia_plan_create — ordering and conditioning sets (Algorithm 1, permutation and
+ * nearest-neighbour loop; Sec. V-A for the orderings).
+ *   xy_host : n x 2 doubles, row-major (x_k, y_k) in the caller's ORIGINAL order.
+ *   n       : number of locations, 1 <= n <= 2^31 - 1.
+ *   m       : conditioning-set size, 1 <= m <= VECCHIA_MAX_M; location i (0-based,
+ *             ordered) conditions on m_i = min(i, m) points.
+ *   order   : VECCHIA_ORDER_*.  RANDOM: Fisher–Yates (i from n-1 down to 1, swap with
+ *             j = splitmix64() mod (i+1)), splitmix64 state initialised to `seed`.
+ *             MAXMIN: first the point nearest the centroid, then repeatedly the point
+ *             whose minimum squared distance to those chosen is largest; ties to the
+ *             lowest original index.  GIVEN: perm_in.
+ *   perm_in : n int64 (host), a permutation of 0..n-1, perm_in[k] = original index of
+ *             the k-th ordered location; only read for ORDER_GIVEN (else may be NULL).
+ *   stream  : stream for the GPU neighbour search and uploads.
+ *   out     : receives the plan handle.
+ * Conditioning sets: J_i = the m_i previously ordered points with the smallest
+ * (d^2, ordered index), d^2 = round(round(dx*dx) + round(dy*dy)), computed on the GPU.
+ * Synchronous: returns after the plan is complete.  Errors: EINVAL (n, m, order,
+ * non-finite xy, perm_in not a permutation), ENOMEM, ECUDA.
+ */
+int vecchia_plan_create(const double* xy_host, int64_t n, int32_t m, int order, uint64_t seed,
+                        const int64_t* perm_in, void* stream, vecchia_plan_t* out);
+
+/* Frees every device and host resource of the plan (NULL is ignored). */
+void vecchia_plan_destroy(vecchia_plan_t plan);
+
+/* n and m of the plan. */
+int vecchia_plan_size(vecchia_plan_t plan, int64_t* n, int32_t* m);
+
+/* perm_out (host, n int64): perm_out[k] = original index of the k-th ordered location. */
+int vecchia_plan_perm(vecchia_plan_t plan, int64_t* perm_out);
+
+/*
+ * nbr_out (host, n x m int32, row-major by ordered location): the conditioning set J_i
+ * as ORDERED indices, ascending in (d^2, index), padded with -1 after m_i entries.
+ * Synchronous (device-to-host copy).
+ */
+int vecchia_plan_neighbors(vecchia_plan_t plan, int32_t* nbr_out);
+
+/*
+ * vecchia_loglik — the Vecchia log-likelihood (Algorithm 1 output l).
+ *   y_dev   : n doubles on the device, in the ORIGINAL location order.
+ *   theta   : host double[4] {sigma2 > 0, beta > 0, nu > 0, tau2 >= 0}, all finite.
+ *   out_dev : 1 double on the device: l.
+ * Asynchronous on `stream`.  Errors returned: EINVAL (bad theta, NULL pointers),
+ * ECUDA.  A non-positive-definite block makes out_dev NaN (see
+ * vecchia_last_error_location).
+ */
+int vecchia_loglik(vecchia_plan_t plan, const double* y_dev, const double theta[4], double* out_dev,
+                   void* stream);
+
+/*
+ * vecchia_loglik_grad — l and its gradient (not in the paper: the adjoint of Algorithm 1
+ * with respect to sigma2, beta and tau2, recomputing each block's factor).
+ *   out_dev : 4 doubles on the device: {l, dl/dsigma2, dl/dbeta, dl/dtau2}.
+ * Same arguments, asynchrony and errors as vecchia_loglik.
+ */
+int vecchia_loglik_grad(vecchia_plan_t plan, const double* y_dev, const double theta[4],
+                        double* out_dev, void* stream);
+
+/*
+ * vecchia_loglik_terms — the per-location terms l_i (Algorithm 1, univariate Gaussian
+ * terms) and, if want_grad, their gradients, indexed by ORDERED location.
+ *   terms_dev : n x (want_grad ? 4 : 1) doubles on the device, row-major:
+ *               {l_i[, dl_i/dsigma2, dl_i/dbeta, dl_i/dtau2]}.
+ * Same arguments, asynchrony and errors as vecchia_loglik.
+ */
+int vecchia_loglik_terms(vecchia_plan_t plan, const double* y_dev, const double theta[4],
+                         int want_grad, double* terms_dev, void* stream);
+
+/*
+ * vecchia_matern — the covariance of Eq. (2) and its beta-derivative, evaluated by the
+ * same device code the likelihood kernels use.
+ *   d_dev        : count distances (>= 0) on the device.
+ *   c_dev        : count doubles on the device: C(d) (sigma2 at d = 0, without nugget).
+ *   dcdbeta_dev  : count doubles on the device (may be NULL): dC/dbeta(d).
+ * Asynchronous on `stream`.  Errors: EINVAL, ECUDA.
+ */
+int vecchia_matern(const double* d_dev, int64_t count, const double theta[4], double* c_dev,
+                   double* dcdbeta_dev, void* stream);
+
+/*
+ * vecchia_last_error_location — synchronises the stream of the plan's last call and
+ * reports the first ordered location whose block was not positive definite in that
+ * call (*loc = -1 if none).  Returns ENOTPD if there was one, else OK.
+ */
+int vecchia_last_error_location(vecchia_plan_t plan, int64_t* loc);
+
+/* Static, NUL-terminated description of a status code. */
+const char* vecchia_strerror(int code);
+
+/*
+ * vecchia_fp64_peak — measures this GPU's sustained FP64 fused-multiply-add rate with a
+ * register-resident DFMA chain kernel (the denominator of the library's fraction-of-
+ * peak figures).  *gflops_out receives GFLOP/s (2 flops per DFMA).  Synchronous.
+ */
+int vecchia_fp64_peak(double* gflops_out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VECCHIA_H */

@@ -1,0 +1,85 @@
+// Shared definitions of the Vecchia CUDA library: status codes, the plan object,
+// covariance-table geometry and small device helpers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/vecchia.h"
+
+namespace vecchia {
+
+// ------------------------------------------------------------------ table geometry
+// The Matérn correlation rho(u) = C(d)/sigma2 is tabulated in u = (d/beta)^2 as
+// piecewise polynomials: for u in [2^e, 2^(e+1)), e in [kELo, kEHi), the octave is
+// cut into 2^kSub equal sub-intervals, each carrying a degree-kDeg polynomial in the
+// local variable t in [-1, 1).  Interval index and t come straight from the bits of u.
+constexpr int kELo = -30;
+constexpr int kEHi = 20;
+constexpr int kSub = 3;
+constexpr int kDeg = 9;
+constexpr int kNCoef = kDeg + 1;
+constexpr int kNInt = (kEHi - kELo) << kSub;
+// Small-u constants stored after the coefficients: kind, nu, a1, G, b0, b1, I(0).
+constexpr int kNConst = 8;
+constexpr int kTableDoubles = kNInt * kNCoef + kNConst;
+
+// Largest bordered block: m + 2 rows (m neighbours, the location, the data border).
+constexpr int kMaxM = VECCHIA_MAX_M;
+constexpr int kMaxK = kMaxM + 1;
+
+struct Plan {
+  int64_t n = 0;
+  int32_t m = 0;
+  int device = 0;
+  double* d_xy = nullptr;     // n x 2, original order
+  int32_t* d_nbr = nullptr;   // n x m, ORIGINAL indices of J_i, -1 padded (ordered rows)
+  int32_t* d_self = nullptr;  // n, original index of ordered location i
+  int64_t* h_perm = nullptr;  // n, host copy of the ordering
+  int32_t* d_inv = nullptr;   // n, ordered position of each original index
+  // reusable scratch
+  double* d_partial = nullptr;  // per-warp partial sums
+  int64_t partial_cap = 0;
+  unsigned long long* d_errloc = nullptr;  // first failing location (ULLONG_MAX = none)
+  cudaStream_t last_stream = nullptr;
+  // covariance tables, cached by nu
+  static constexpr int kCache = 4;
+  double cache_nu[kCache] = {0, 0, 0, 0};
+  double* cache_tab[kCache] = {nullptr, nullptr, nullptr, nullptr};
+  int cache_next = 0;
+};
+
+// ------------------------------------------------------------------ device helpers
+__device__ __forceinline__ double rcp_newton(double d) {
+  // Reciprocal: hardware approximation of 1/d (about 20 correct bits), then one
+  // cubically convergent Newton step y <- y (1 + e + e^2), e = 1 - d y.
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(d));
+  const double e = fma(-d, y, 1.0);
+  const double e2 = fma(e, e, e);
+  return fma(y, e2, y);
+}
+
+// True iff d is a positive finite double, decided on the bit pattern (no FP64 op).
+__device__ __forceinline__ bool positive_finite(double d) {
+  const long long b = __double_as_longlong(d);
+  return b > 0 && b < 0x7FF0000000000000LL;
+}
+
+struct Neumaier {
+  double s = 0.0, c = 0.0;
+  __device__ __forceinline__ void add(double x) {
+    const double t = s + x;
+    if (fabs(s) >= fabs(x)) c += (s - t) + x; else c += (x - t) + s;
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return s + c; }
+};
+
+}  // namespace vecchia
+
+#define VECCHIA_CUDA_TRY(expr)                        \
+  do {                                                \
+    cudaError_t _e = (expr);                          \
+    if (_e != cudaSuccess) return VECCHIA_ECUDA;      \
+  } while (0)

@@ -1,0 +1,204 @@
+// Construction of the per-nu Matérn correlation table and the stand-alone covariance
+// evaluator (vecchia_matern).
+//
+// rho(u) = 2^{1-nu}/Gamma(nu) x^nu K_nu(x), u = x^2, is computed at the table nodes from
+// the integral representation K_nu(z) = (z/2)^nu / 2 int_0^inf exp(-t - z^2/(4t)) t^{-nu-1} dt
+// (DLMF 10.32.10).  Substituting t = z^2/(4s) and s = e^tau gives
+//   rho(u) = I(u) / I(0),   I(u) = int_R exp(nu tau - e^tau - (u/4) e^{-tau}) dtau,
+// (I(0) = Gamma(nu)).  The integrand is analytic in the strip |Im tau| < pi/2 and decays
+// double-exponentially, so the trapezoidal rule converges geometrically; the step is
+// set from the curvature at the peak and from nu, and terms are summed with Neumaier
+// compensation until they fall below e^-45 of the peak.
+// Each interval's polynomial is the degree-kDeg Chebyshev interpolant at the
+// first-kind Chebyshev points, converted to monomials in t.
+#include <algorithm>
+#include <cmath>
+#include <mutex>
+#include <vector>
+
+#include "common.cuh"
+#include "matern.cuh"
+
+namespace vecchia {
+
+__device__ double quad_I(double u, double nu) {
+  const double a = 0.25 * u;
+  const double et = 0.5 * (nu + sqrt(nu * nu + 4.0 * a));  // e^tau at the peak
+  const double tc = log(et);
+  const double curv = et + a / et;                          // -(log integrand)'' at the peak
+  const double h = fmin(0.2, fmin(0.6 / sqrt(curv), 0.3 / fmax(nu, 1.0)));
+  const double lpeak = nu * tc - et - a / et;
+  Neumaier acc;
+  for (int side = 0; side < 2; ++side) {
+    for (int k = side; k < 200000; ++k) {
+      const double tau = side == 0 ? tc + k * h : tc - k * h;
+      const double e = exp(tau);
+      const double lv = nu * tau - e - a / e;
+      acc.add(exp(lv - lpeak));
+      if (lv - lpeak < -45.0 && k > 3) break;
+    }
+  }
+  return acc.value() * h * exp(lpeak);
+}
+
+// One thread: I(0) and the small-u expansion constants.
+__global__ void matern_const_kernel(double nu, double* tab) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double* c = tab + kNInt * kNCoef;
+  const bool integer = (nu == floor(nu));
+  long long kind = integer ? (nu == 1.0 ? 1 : 2) : 0;
+  c[0] = __longlong_as_double(kind);
+  c[1] = nu;
+  if (integer) {
+    c[2] = nu == 1.0 ? 0.0 : -0.25 / (nu - 1.0);
+    c[3] = c[4] = c[5] = 0.0;
+  } else {
+    c[2] = 0.25 / (1.0 - nu);
+    c[3] = tgamma(1.0 - nu);
+    c[4] = 1.0 / tgamma(1.0 + nu);
+    c[5] = 0.25 / tgamma(2.0 + nu);
+  }
+  c[6] = quad_I(0.0, nu);
+  c[7] = 0.0;
+}
+
+// One block of 32 threads per interval.
+__global__ void matern_fit_kernel(double nu, double* tab) {
+  __shared__ double f[kNCoef], cheb[kNCoef], tm[kNCoef][kNCoef];
+  const int idx = blockIdx.x;
+  const int e = kELo + (idx >> kSub);
+  const int j = idx & ((1 << kSub) - 1);
+  const int tid = threadIdx.x;
+  const double I0 = tab[kNInt * kNCoef + 6];
+  const double scale = ldexp(1.0, e);
+  const double mid = scale * (1.0 + (2.0 * j + 1.0) / 16.0);
+  const double hw = scale / 16.0;
+  if (tid < kNCoef) {
+    const double tn = cospi((tid + 0.5) / kNCoef);
+    f[tid] = quad_I(mid + hw * tn, nu) / I0;
+  }
+  if (tid == 0) {
+    // Monomial coefficients of T_0..T_kDeg (exact small integers).
+    for (int k = 0; k < kNCoef; ++k)
+      for (int q = 0; q < kNCoef; ++q) tm[k][q] = 0.0;
+    tm[0][0] = 1.0;
+    tm[1][1] = 1.0;
+    for (int k = 2; k < kNCoef; ++k)
+      for (int q = 0; q < kNCoef; ++q)
+        tm[k][q] = (q > 0 ? 2.0 * tm[k - 1][q - 1] : 0.0) - tm[k - 2][q];
+  }
+  __syncthreads();
+  if (tid < kNCoef) {
+    double s = 0.0;
+    for (int q = 0; q < kNCoef; ++q) s += f[q] * cospi(tid * (q + 0.5) / kNCoef);
+    cheb[tid] = (tid == 0 ? 1.0 : 2.0) * s / kNCoef;
+  }
+  __syncthreads();
+  if (tid < kNCoef) {
+    double a = 0.0;
+    for (int k = kNCoef - 1; k >= 0; --k) a += cheb[k] * tm[k][tid];
+    tab[idx * kNCoef + tid] = a;
+  }
+}
+
+// ------------------------------------------------------------------ table cache
+namespace {
+struct TableEntry {
+  int device = -1;
+  double nu = 0.0;
+  double* d_tab = nullptr;
+  cudaEvent_t ready = nullptr;
+  unsigned long long last_use = 0;
+};
+std::mutex g_mu;
+std::vector<TableEntry> g_tables;
+unsigned long long g_clock = 0;
+constexpr size_t kMaxTables = 16;
+}  // namespace
+
+// Returns (building on `stream` if needed) the device table for nu on the current device.
+int get_matern_table(double nu, cudaStream_t stream, const double** out) {
+  int dev = 0;
+  VECCHIA_CUDA_TRY(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_mu);
+  for (auto& t : g_tables) {
+    if (t.device == dev && t.nu == nu) {
+      VECCHIA_CUDA_TRY(cudaStreamWaitEvent(stream, t.ready, 0));
+      t.last_use = ++g_clock;
+      *out = t.d_tab;
+      return VECCHIA_OK;
+    }
+  }
+  double* d = nullptr;
+  if (cudaMalloc(&d, sizeof(double) * kTableDoubles) != cudaSuccess) return VECCHIA_ENOMEM;
+  cudaEvent_t ev;
+  if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+    cudaFree(d);
+    return VECCHIA_ECUDA;
+  }
+  TableEntry* slot = nullptr;
+  if (g_tables.size() < kMaxTables) {
+    g_tables.emplace_back();
+    slot = &g_tables.back();
+  } else {
+    // Evict the least recently used table once no kernel can still be reading it.
+    slot = &*std::min_element(g_tables.begin(), g_tables.end(),
+                              [](const TableEntry& a, const TableEntry& b) { return a.last_use < b.last_use; });
+    cudaDeviceSynchronize();
+    cudaFree(slot->d_tab);
+    cudaEventDestroy(slot->ready);
+    *slot = TableEntry();
+  }
+  matern_const_kernel<<<1, 32, 0, stream>>>(nu, d);
+  matern_fit_kernel<<<kNInt, 32, 0, stream>>>(nu, d);
+  VECCHIA_CUDA_TRY(cudaGetLastError());
+  VECCHIA_CUDA_TRY(cudaEventRecord(ev, stream));
+  slot->device = dev;
+  slot->nu = nu;
+  slot->d_tab = d;
+  slot->ready = ev;
+  slot->last_use = ++g_clock;
+  *out = d;
+  return VECCHIA_OK;
+}
+
+// ------------------------------------------------------------------ vecchia_matern
+__global__ void matern_eval_kernel(const double* __restrict__ d, int64_t count, double sigma2,
+                                   double beta, const double* __restrict__ tab, double* __restrict__ c,
+                                   double* __restrict__ dc) {
+  const MaternConst mc = load_matern_const(tab);
+  const double ib = 1.0 / beta;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double x = d[i] * ib;
+    const double u = x * x;
+    double rho, h;
+    rho_eval_d(u, tab, mc, rho, h);
+    c[i] = sigma2 * rho;
+    if (dc) dc[i] = -2.0 * sigma2 * ib * h;
+  }
+}
+
+bool theta_ok(const double* th) {
+  if (!th) return false;
+  for (int k = 0; k < 4; ++k)
+    if (!std::isfinite(th[k])) return false;
+  return th[0] > 0.0 && th[1] > 0.0 && th[2] > 0.0 && th[3] >= 0.0;
+}
+
+}  // namespace vecchia
+
+extern "C" int vecchia_matern(const double* d_dev, int64_t count, const double theta[4], double* c_dev,
+                              double* dcdbeta_dev, void* stream) {
+  using namespace vecchia;
+  if (count < 0 || (count > 0 && (!d_dev || !c_dev)) || !theta_ok(theta)) return VECCHIA_EINVAL;
+  if (count == 0) return VECCHIA_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  const double* tab = nullptr;
+  int rc = get_matern_table(theta[2], s, &tab);
+  if (rc) return rc;
+  const int64_t blocks = std::min<int64_t>((count + 255) / 256, 4096);
+  matern_eval_kernel<<<(int)blocks, 256, 0, s>>>(d_dev, count, theta[0], theta[1], tab, c_dev, dcdbeta_dev);
+  VECCHIA_CUDA_TRY(cudaGetLastError());
+  return VECCHIA_OK;
+}

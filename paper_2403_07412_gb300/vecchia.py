@@ -1,0 +1,232 @@
+"""Python binding of the C ABI in include/vecchia.h (argument marshalling only).
+
+Every computation runs in ``libvecchia.so``; PyTorch supplies device memory and the
+current CUDA stream.  The library is loaded from this package directory and its
+absence is an error: there is no CPU fallback.
+
+The entry points keep the C names: :func:`vecchia_plan_create` (wrapped by
+:class:`Plan`), :func:`vecchia_loglik`, :func:`vecchia_loglik_grad`,
+:func:`vecchia_loglik_terms`, :func:`vecchia_matern`, :func:`vecchia_fp64_peak`;
+:class:`VecchiaLogLik` is the ``torch.autograd.Function`` over theta.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libvecchia.so")
+
+OK, EINVAL, ENOTPD, ECUDA, ETIMEOUT, ENOMEM = range(6)
+ORDER_GIVEN, ORDER_RANDOM, ORDER_MAXMIN = 0, 1, 2
+MAX_M = 63
+
+_lock = threading.Lock()
+_lib = None
+
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_i32 = ctypes.c_int32
+_dp = ctypes.POINTER(ctypes.c_double)
+
+# name -> (restype, argtypes); the C ABI as declared in include/vecchia.h
+SIGNATURES = {
+    "vecchia_plan_create": (ctypes.c_int, [_dp, _i64, _i32, ctypes.c_int, ctypes.c_uint64,
+                                           ctypes.POINTER(_i64), _vp, ctypes.POINTER(_vp)]),
+    "vecchia_plan_destroy": (None, [_vp]),
+    "vecchia_plan_size": (ctypes.c_int, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i32)]),
+    "vecchia_plan_perm": (ctypes.c_int, [_vp, ctypes.POINTER(_i64)]),
+    "vecchia_plan_neighbors": (ctypes.c_int, [_vp, ctypes.POINTER(_i32)]),
+    "vecchia_loglik": (ctypes.c_int, [_vp, _vp, _dp, _vp, _vp]),
+    "vecchia_loglik_grad": (ctypes.c_int, [_vp, _vp, _dp, _vp, _vp]),
+    "vecchia_loglik_terms": (ctypes.c_int, [_vp, _vp, _dp, ctypes.c_int, _vp, _vp]),
+    "vecchia_matern": (ctypes.c_int, [_vp, _i64, _dp, _vp, _vp, _vp]),
+    "vecchia_last_error_location": (ctypes.c_int, [_vp, ctypes.POINTER(_i64)]),
+    "vecchia_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "vecchia_fp64_peak": (ctypes.c_int, [_dp, _vp]),
+}
+
+
+class VecchiaError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        msg = lib().vecchia_strerror(code).decode() if _lib is not None else str(code)
+        super().__init__(f"{where}: {msg} (status {code})")
+        self.code = code
+
+
+def lib():
+    """The loaded CUDA library; raises if ``libvecchia.so`` has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                                   "paper_2403_07412_gb300.build.build() (nvcc, sm_103a)")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in SIGNATURES.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+        return _lib
+
+
+def _check(code: int, where: str) -> None:
+    if code != OK:
+        raise VecchiaError(code, where)
+
+
+def _stream(stream=None) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _theta(theta) -> ctypes.Array:
+    t = [float(v) for v in (theta.tolist() if hasattr(theta, "tolist") else theta)]
+    if len(t) != 4:
+        raise ValueError("theta must be (sigma2, beta, nu, tau2)")
+    return (ctypes.c_double * 4)(*t)
+
+
+def _dev_f64(x: torch.Tensor, n: int, name: str) -> torch.Tensor:
+    if not (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == torch.float64):
+        raise TypeError(f"{name} must be a CUDA float64 tensor")
+    if x.numel() != n or not x.is_contiguous():
+        raise ValueError(f"{name} must be contiguous with {n} elements")
+    return x
+
+
+class Plan:
+    """Ordering and conditioning sets for one set of locations (vecchia_plan_create)."""
+
+    def __init__(self, xy, m: int, order: int = ORDER_RANDOM, seed: int = 0, perm=None, stream=None):
+        xy = np.ascontiguousarray(np.asarray(xy, dtype=np.float64).reshape(-1, 2))
+        self.n = int(xy.shape[0])
+        self.m = int(m)
+        h = _vp()
+        pin = None
+        if order == ORDER_GIVEN:
+            pin = np.ascontiguousarray(np.asarray(perm, dtype=np.int64))
+        rc = lib().vecchia_plan_create(xy.ctypes.data_as(_dp), self.n, self.m, int(order),
+                                       ctypes.c_uint64(int(seed) & 0xFFFFFFFFFFFFFFFF),
+                                       pin.ctypes.data_as(ctypes.POINTER(_i64)) if pin is not None else None,
+                                       _vp(_stream(stream)), ctypes.byref(h))
+        _check(rc, "vecchia_plan_create")
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().vecchia_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def perm(self) -> np.ndarray:
+        out = np.empty(self.n, dtype=np.int64)
+        _check(lib().vecchia_plan_perm(self._h, out.ctypes.data_as(ctypes.POINTER(_i64))), "vecchia_plan_perm")
+        return out
+
+    def neighbors(self) -> np.ndarray:
+        out = np.empty((self.n, self.m), dtype=np.int32)
+        _check(lib().vecchia_plan_neighbors(self._h, out.ctypes.data_as(ctypes.POINTER(_i32))),
+               "vecchia_plan_neighbors")
+        return out
+
+    def last_error_location(self) -> int:
+        loc = _i64(-1)
+        lib().vecchia_last_error_location(self._h, ctypes.byref(loc))
+        return int(loc.value)
+
+
+def vecchia_loglik(plan: Plan, y: torch.Tensor, theta, out: torch.Tensor | None = None, stream=None):
+    y = _dev_f64(y, plan.n, "y")
+    if out is None:
+        out = torch.empty(1, dtype=torch.float64, device=y.device)
+    rc = lib().vecchia_loglik(plan.handle, _vp(y.data_ptr()), _theta(theta), _vp(out.data_ptr()),
+                              _vp(_stream(stream)))
+    _check(rc, "vecchia_loglik")
+    return out
+
+
+def vecchia_loglik_grad(plan: Plan, y: torch.Tensor, theta, out: torch.Tensor | None = None, stream=None):
+    y = _dev_f64(y, plan.n, "y")
+    if out is None:
+        out = torch.empty(4, dtype=torch.float64, device=y.device)
+    rc = lib().vecchia_loglik_grad(plan.handle, _vp(y.data_ptr()), _theta(theta), _vp(out.data_ptr()),
+                                   _vp(_stream(stream)))
+    _check(rc, "vecchia_loglik_grad")
+    return out
+
+
+def vecchia_loglik_terms(plan: Plan, y: torch.Tensor, theta, want_grad: bool = False,
+                         out: torch.Tensor | None = None, stream=None):
+    y = _dev_f64(y, plan.n, "y")
+    w = 4 if want_grad else 1
+    if out is None:
+        out = torch.empty((plan.n, w), dtype=torch.float64, device=y.device)
+    rc = lib().vecchia_loglik_terms(plan.handle, _vp(y.data_ptr()), _theta(theta), 1 if want_grad else 0,
+                                    _vp(out.data_ptr()), _vp(_stream(stream)))
+    _check(rc, "vecchia_loglik_terms")
+    return out if want_grad else out[:, 0]
+
+
+def vecchia_matern(d: torch.Tensor, theta, with_dbeta: bool = True, stream=None):
+    d = _dev_f64(d, d.numel(), "d")
+    c = torch.empty_like(d)
+    dc = torch.empty_like(d) if with_dbeta else None
+    rc = lib().vecchia_matern(_vp(d.data_ptr()), d.numel(), _theta(theta), _vp(c.data_ptr()),
+                              _vp(dc.data_ptr()) if dc is not None else None, _vp(_stream(stream)))
+    _check(rc, "vecchia_matern")
+    return (c, dc) if with_dbeta else c
+
+
+def vecchia_fp64_peak(stream=None) -> float:
+    g = ctypes.c_double(0.0)
+    _check(lib().vecchia_fp64_peak(ctypes.byref(g), _vp(_stream(stream))), "vecchia_fp64_peak")
+    return float(g.value)
+
+
+class VecchiaLogLik(torch.autograd.Function):
+    """l(theta) as a differentiable function of theta = (sigma2, beta, nu, tau2).
+
+    Backward uses the library's adjoint for (sigma2, beta, tau2) and a central finite
+    difference of the forward kernel for nu (step ``nu_step`` relative).
+    """
+
+    @staticmethod
+    def forward(ctx, theta: torch.Tensor, plan: Plan, y: torch.Tensor, nu_step: float = 1e-6):
+        th = theta.detach().to("cpu", torch.float64)
+        g = vecchia_loglik_grad(plan, y, th)
+        ctx.plan, ctx.y, ctx.nu_step = plan, y, nu_step
+        ctx.save_for_backward(theta.detach())
+        ctx.g = g
+        return g[0:1].clone().reshape(()).to(theta.device)
+
+    @staticmethod
+    def backward(ctx, gout):
+        (theta,) = ctx.saved_tensors
+        th = theta.to("cpu", torch.float64)
+        nu = float(th[2])
+        h = ctx.nu_step * nu
+        tp, tm = th.clone(), th.clone()
+        tp[2] = nu + h
+        tm[2] = nu - h
+        lp = vecchia_loglik(ctx.plan, ctx.y, tp)
+        lm = vecchia_loglik(ctx.plan, ctx.y, tm)
+        dnu = (lp - lm) / (2.0 * h)
+        g = ctx.g
+        grad = torch.stack([g[1], g[2], dnu[0], g[3]]).to(theta.device, theta.dtype)
+        return gout * grad, None, None, None
