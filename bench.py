@@ -1,0 +1,354 @@
+"""Benchmark: Vecchia log-likelihood + gradient throughput on the GPU.
+
+Workload (default): n = 1,000,000 locations from a 20-component Gaussian mixture in the
+unit square, random-Fourier-feature Matérn field with nu = 1.0 (general Bessel K),
+sigma2 = 1, beta = 0.02, tau2 = 0.01, maxmin ordering, m = 60.  One step = one call of
+vecchia_loglik_grad over all n locations (log-likelihood and d/d(sigma2, beta, tau2)).
+
+Prints one JSON line.  ``value`` = locations per second over the whole job, timed with
+CUDA events on the launching stream with the inputs resident in HBM; ``e2e`` repeats the
+measurement through the same C-ABI call with the field copied from pinned host memory
+and the result copied back every step.  ``roofline`` rates the dominant kernel
+(vecchia_lik_kernel, fwd+adjoint) against the FP64 FMA peak measured in the same run.
+``cpu_baseline`` times the CPU oracle on a bounded sample of the same workload.
+
+Multi-GPU (torchrun, N > 1): every rank evaluates its own independent field of the same
+shape (weak scaling; no collective on the data path); value = N * n / max step time.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "vecchia-matern-gmm1M-maxmin-m60-nu1.0-fwd+grad"
+METRIC = "Vecchia loglik+grad locations/sec (n=1M, m=60) and fraction of FP64 peak"
+
+
+def la_flops(n: int, m: int, grad: bool) -> float:
+    """Algorithmic FP64 flops of one evaluation: per location k = m_i + 1,
+    k^3/3 + k^2/2 + k/6 (Cholesky) + k^2 (two triangular solves); the adjoint adds
+    two unit triangular solves of size m_i (2 m_i^2)."""
+    i = np.arange(n, dtype=np.float64)
+    mi = np.minimum(i, m)
+    k = mi + 1
+    f = k ** 3 / 3 + k ** 2 / 2 + k / 6 + k ** 2
+    if grad:
+        f = f + 2 * mi ** 2
+    return float(f.sum())
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: str):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", self.gpu], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_workload(n, device, rank):
+    from paper_2403_07412_gb300 import datagen
+
+    seed = datagen.BASE_SEED + 5 + 1000 * rank
+    xy = datagen.gmm_locations(n, seed)
+    theta = (1.0, 0.02, 1.0, 0.01)
+    y = datagen.field_rff(xy, theta, seed + 1000, device=device)
+    return xy, y, theta
+
+
+def cpu_baseline(xy, y, theta, m, budget_s):
+    """The oracle, as it stands, on a bounded random sample of rows of the same workload
+    (its own random ordering and brute-force conditioning sets; neighbour search untimed)."""
+    import oracle
+
+    oracle.build()
+    n = xy.shape[0]
+    perm = oracle.order_random(n, 99)
+    xo, yo = xy[perm], y[perm]
+    rng = np.random.default_rng(0)
+    probe = np.sort(rng.choice(np.arange(m + 1, n), 64, replace=False))
+    nb = oracle.knn_rows(xo, m, probe)
+    t0 = time.perf_counter()
+    oracle.vecchia_rows(xo, yo, m, theta, rows=probe, nbr=nb, want_grad=True)
+    per_row = (time.perf_counter() - t0) / probe.size
+    rows_n = int(max(64, min(200_000, budget_s / max(per_row, 1e-7))))
+    rows = np.sort(rng.choice(np.arange(m + 1, n), rows_n, replace=False))
+    nb = oracle.knn_rows(xo, m, rows)
+    t0 = time.perf_counter()
+    oracle.vecchia_rows(xo, yo, m, theta, rows=rows, nbr=nb, want_grad=True)
+    dt = time.perf_counter() - t0
+    return {"value": rows_n / dt, "unit": "locations/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{rows_n} random locations (i > m) of the same 1M-location workload, loglik+grad, "
+                      f"oracle's own random ordering and brute-force neighbour sets (untimed); {dt:.1f} s wall"}
+
+
+def run_reference(args, rank, world):
+    """--impl reference: the CPU oracle as it stands, timed per step on a bounded sample."""
+    if rank != 0:
+        return
+    import oracle
+
+    oracle.build()
+    n, m = args.n, 60
+    xy, y, theta = make_workload(n, None, 0)
+    perm = oracle.order_random(n, 99)
+    xo, yo = xy[perm], y[perm]
+    rng = np.random.default_rng(0)
+    probe = np.sort(rng.choice(np.arange(m + 1, n), 64, replace=False))
+    nb = oracle.knn_rows(xo, m, probe)
+    t0 = time.perf_counter()
+    oracle.vecchia_rows(xo, yo, m, theta, rows=probe, nbr=nb, want_grad=True)
+    per_row = (time.perf_counter() - t0) / probe.size
+    total_steps = args.steps + args.warmup
+    rows_n = int(max(32, min(100_000, args.ref_budget / total_steps / max(per_row, 1e-7))))
+    rows = np.sort(rng.choice(np.arange(m + 1, n), rows_n, replace=False))
+    nb = oracle.knn_rows(xo, m, rows)
+    times = []
+    for s in range(total_steps):
+        t0 = time.perf_counter()
+        oracle.vecchia_rows(xo, yo, m, theta, rows=rows, nbr=nb, want_grad=True)
+        if s >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    per_step = statistics.median(times)
+    value = rows_n / per_step
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "locations/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": n, "m": m, "ordering": "random (oracle's own)",
+                   "theta": list(theta), "sample_locations_per_step": rows_n},
+        "cpu_baseline": {"value": value, "unit": "locations/s", "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": f"{rows_n} random locations of the {n}-location workload per step"},
+        "e2e": {"value": value, "unit": "locations/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--n", type=int, default=1_000_000)
+    ap.add_argument("--m", type=int, default=60)
+    ap.add_argument("--order", default="maxmin", choices=["maxmin", "random"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle wall time")
+    ap.add_argument("--ref-budget", type=float, default=90.0, help="seconds for the whole reference run")
+    ap.add_argument("--fwd", action="store_true", help="time the forward-only kernel instead")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.init_process_group("gloo")
+        run_reference(args, rank, world)
+        return
+
+    import torch
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    from paper_2403_07412_gb300 import build as vbuild
+
+    if rank == 0:
+        vbuild.build()
+    if dist is not None:
+        dist.barrier()
+    from paper_2403_07412_gb300 import vecchia as V
+
+    dev = torch.device("cuda", local)
+    n, m = args.n, args.m
+    xy, y, theta = make_workload(n, dev, rank)
+    t0 = time.perf_counter()
+    plan = V.Plan(xy, m, order=V.ORDER_MAXMIN if args.order == "maxmin" else V.ORDER_RANDOM, seed=5)
+    torch.cuda.synchronize()
+    plan_s = time.perf_counter() - t0
+    yd = torch.as_tensor(y, device=dev)
+    out = torch.empty(4, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    call = V.vecchia_loglik if args.fwd else V.vecchia_loglik_grad
+    peak_gflops = V.vecchia_fp64_peak()
+
+    for _ in range(args.warmup):
+        call(plan, yd, theta, out=out)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    gpu_index = os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0] if world == 1 else str(local)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(gpu_index) as clk:
+        time.sleep(0.3)
+        g0 = torch.cuda.Event(enable_timing=True)
+        g1 = torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        for s in range(args.steps):
+            ev[s][0].record(stream)
+            call(plan, yd, theta, out=out)
+            ev[s][1].record(stream)
+        g1.record(stream)
+        torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    total_ms = g0.elapsed_time(g1)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    if dist is not None:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * n / (ms_per_step * 1e-3)
+    res = out.cpu().numpy()
+    ok = bool(np.all(np.isfinite(res)))
+
+    # end to end: field from pinned host memory, result back to the host, every step
+    y_host = torch.as_tensor(y).pin_memory()
+    res_host = torch.empty(4, dtype=torch.float64).pin_memory()
+    for _ in range(2):
+        yd.copy_(y_host, non_blocking=True)
+        call(plan, yd, theta, out=out)
+        res_host.copy_(out, non_blocking=True)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        yd.copy_(y_host, non_blocking=True)
+        call(plan, yd, theta, out=out)
+        res_host.copy_(out, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / args.steps
+    if dist is not None:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    flops = la_flops(n, m, grad=not args.fwd)
+    kern_ms = statistics.mean(step_ms)
+    achieved = flops / (kern_ms * 1e-3) / 1e12
+    peak = peak_gflops / 1e3
+    traffic_path = os.path.join(ROOT, "profiles", "traffic.json")
+    traffic = None
+    if os.path.exists(traffic_path):
+        try:
+            tj = json.load(open(traffic_path))
+            key = "fwd" if args.fwd else "grad"
+            if tj.get("n") == n and tj.get("m") == m and key in tj:
+                traffic = tj[key]
+        except Exception:
+            traffic = None
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "locations/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_per_step,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {
+            "workload": WORKLOAD if not args.fwd else WORKLOAD.replace("fwd+grad", "fwd"),
+            "n": n, "m": m, "ordering": args.order, "theta": list(theta),
+            "locations": "20-component Gaussian mixture in [0,1]^2",
+            "field": "random Fourier features, 4096, Matern nu=1.0",
+            "l2": "inputs exceed L2 (264 MB per step: 240 MB neighbour table, 16 MB coordinates, 8 MB field)",
+            "plan_seconds": round(plan_s, 3),
+            "result_finite": ok,
+            "parallelism": f"{world} independent fields (one per GPU)",
+        },
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "vecchia_lik_kernel<true>" if not args.fwd else "vecchia_lik_kernel<false>",
+                     "flops_per_launch": flops,
+                     "peak_source": "FP64 DFMA-chain kernel measured in this run (vecchia_fp64_peak)"},
+        "e2e": {"value": world * n / (e2e_ms * 1e-3), "unit": "locations/s",
+                "h2d_bytes_per_step": int(y_host.numel() * 8), "d2h_bytes_per_step": int(res_host.numel() * 8)},
+        "gpu_launches": 2 * args.steps,
+        "clocks": clk.summary(),
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(xy, y, theta, m, args.cpu_budget)
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

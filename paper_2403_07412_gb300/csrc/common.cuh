@@ -18,11 +18,14 @@ constexpr int kELo = -30;
 constexpr int kEHi = 20;
 constexpr int kSub = 3;
 constexpr int kDeg = 9;
-constexpr int kNCoef = kDeg + 1;
 constexpr int kNInt = (kEHi - kELo) << kSub;
-// Small-u constants stored after the coefficients: kind, nu, a1, G, b0, b1, I(0).
+// Per interval: FP64 {c0, c1, c2, c3, c4, c5, 2 c2, 0} and FP32
+// {c6, c7, c8, c9, 3c3, 4c4, 5c5, 6c6, 7c7, 8c8, 9c9, 0} (see matern.cuh).
+constexpr int kNDbl = 8;
+constexpr int kNFlt = 12;
+// Small-u constants stored after the FP64 coefficients: kind, nu, a1, G, b0, b1, I(0).
 constexpr int kNConst = 8;
-constexpr int kTableDoubles = kNInt * kNCoef + kNConst;
+constexpr size_t kTableBytes = sizeof(double) * (kNInt * kNDbl + kNConst) + sizeof(float) * kNInt * kNFlt;
 
 // Largest bordered block: m + 2 rows (m neighbours, the location, the data border).
 constexpr int kMaxM = VECCHIA_MAX_M;

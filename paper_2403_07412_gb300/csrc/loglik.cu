@@ -34,6 +34,7 @@
 // factor already in shared memory (rows m and K of L are L_J^{-1}-scaled v and y_J).
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 
 #include "common.cuh"
 #include "matern.cuh"
@@ -83,7 +84,7 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 template <bool GRAD>
-__global__ void __launch_bounds__(256) vecchia_lik_kernel(const LikArgs a) {
+__global__ void __launch_bounds__(384) vecchia_lik_kernel(const LikArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int m = a.m;
   const int K = m + 1;
@@ -162,19 +163,32 @@ __global__ void __launch_bounds__(256) vecchia_lik_kernel(const LikArgs a) {
       A[o + K - c] = YV[c];
     }
     if (lane == 0) A[0] = 0.0;
-    for (int q = lane; q < L.NP; q += 32) {
-      const uint32_t w = pairs[q];
-      const int r = w & 0xFF, c = (w >> 8) & 0xFF, e = w >> 16;
-      double val = 0.0, hv = 0.0;
-      if (c < mi && (r < mi || r == m)) {
-        const double dx = X[r] - X[c];
-        const double dy = Y[r] - Y[c];
-        const double u = fma(dx, dx, dy * dy);
-        if (GRAD) rho_eval_d(u, a.tab, mc, val, hv);
-        else val = rho_eval(u, a.tab, mc);
+    // Two pairs per lane per iteration so one pair's loads overlap the other's FMAs.
+    for (int q0 = lane; q0 < L.NP; q0 += 64) {
+      const int q1 = q0 + 32;
+      const bool has1 = q1 < L.NP;
+      const uint32_t w0 = pairs[q0];
+      const uint32_t w1 = has1 ? pairs[q1] : w0;
+      const int r0 = w0 & 0xFF, c0 = (w0 >> 8) & 0xFF;
+      const int r1 = w1 & 0xFF, c1 = (w1 >> 8) & 0xFF;
+      const bool v0 = c0 < mi && (r0 < mi || r0 == m);
+      const bool v1 = has1 && c1 < mi && (r1 < mi || r1 == m);
+      const double dx0 = X[r0] - X[c0], dy0 = Y[r0] - Y[c0];
+      const double dx1 = X[r1] - X[c1], dy1 = Y[r1] - Y[c1];
+      const double u0 = fma(dx0, dx0, dy0 * dy0), u1 = fma(dx1, dx1, dy1 * dy1);
+      double val0, hv0 = 0.0, val1, hv1 = 0.0;
+      rho_poly<GRAD>(u0, a.tab, val0, hv0);
+      rho_poly<GRAD>(u1, a.tab, val1, hv1);
+      rho_fix(u0, mc, val0, hv0);
+      rho_fix(u1, mc, val1, hv1);
+      if (!v0) { val0 = 0.0; hv0 = 0.0; }
+      if (!v1) { val1 = 0.0; hv1 = 0.0; }
+      A[w0 >> 16] = val0;
+      if (GRAD) H[q0] = hv0;
+      if (has1) {
+        A[w1 >> 16] = val1;
+        if (GRAD) H[q1] = hv1;
       }
-      A[e] = val;
-      if (GRAD) H[q] = hv;
     }
     __syncwarp();
     // ---- L D L^T over the neighbour columns
@@ -190,11 +204,40 @@ __global__ void __launch_bounds__(256) vecchia_lik_kernel(const LikArgs a) {
         A[oj + r - j] = tv * inv;
       }
       __syncwarp();
+      // Trailing update of the prefix [1, oj), four slots per lane per batch: the next
+      // batch's shared-memory loads are issued before this batch's results are stored.
       const double* Lc = A + oj - j;  // Lc[r] = L[r][j]
-      for (int e = 1 + lane; e < oj; e += 32) {
-        const uint32_t rc = sched[e];
-        const int r = rc & 0xFF, c = rc >> 8;
-        A[e] = fma(-Lc[r], TV[c], A[e]);
+      constexpr int U = 4;
+      double lv[U], tv[U], av[U];
+      int ee[U];
+#pragma unroll
+      for (int k = 0; k < U; ++k) {
+        ee[k] = 1 + lane + 32 * k;
+        const int ek = ee[k] < oj ? ee[k] : 0;
+        const uint32_t rc = sched[ek];
+        lv[k] = Lc[rc & 0xFF];
+        tv[k] = TV[rc >> 8];
+        av[k] = A[ek];
+      }
+      for (int base = 1 + lane; base < oj; base += 32 * U) {
+        double res[U];
+#pragma unroll
+        for (int k = 0; k < U; ++k) res[k] = fma(-lv[k], tv[k], av[k]);
+        int ne[U];
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+          ne[k] = base + 32 * (U + k);
+          const int ek = ne[k] < oj ? ne[k] : 0;
+          const uint32_t rc = sched[ek];
+          lv[k] = Lc[rc & 0xFF];
+          tv[k] = TV[rc >> 8];
+          av[k] = A[ek];
+        }
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+          if (ee[k] < oj) A[ee[k]] = res[k];
+          ee[k] = ne[k];
+        }
       }
       __syncwarp();
     }
@@ -325,7 +368,13 @@ int pick_config(int K, bool grad, LaunchCfg* cfg) {
   VECCHIA_CUDA_TRY(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   const SmemLayout L(K, grad);
   int best_warps = -1;
-  for (int W : {8, 6, 4, 2, 1}) {
+  // Warps per CTA: the candidate giving the most resident warps per SM wins (ties go
+  // to the larger CTA).  VECCHIA_WARPS_PER_CTA forces one value (tuning experiments).
+  const char* fenv = getenv("VECCHIA_WARPS_PER_CTA");
+  const int forced = fenv ? atoi(fenv) : 0;
+  const int cand_all[] = {12, 10, 8, 6, 4, 2, 1};
+  for (int W : cand_all) {
+    if (forced > 0 && W != forced) continue;
     const int bytes = L.bytes(W);
     if (bytes > smem_optin) continue;
     auto kern = grad ? vecchia_lik_kernel<true> : vecchia_lik_kernel<false>;

@@ -10,7 +10,8 @@
 // set from the curvature at the peak and from nu, and terms are summed with Neumaier
 // compensation until they fall below e^-45 of the peak.
 // Each interval's polynomial is the degree-kDeg Chebyshev interpolant at the
-// first-kind Chebyshev points, converted to monomials in t.
+// first-kind Chebyshev points, converted to monomials in t and stored in the split
+// FP64/FP32 layout that matern.cuh evaluates.
 #include <algorithm>
 #include <cmath>
 #include <mutex>
@@ -44,7 +45,7 @@ __device__ double quad_I(double u, double nu) {
 // One thread: I(0) and the small-u expansion constants.
 __global__ void matern_const_kernel(double nu, double* tab) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  double* c = tab + kNInt * kNCoef;
+  double* c = tab + kNInt * kNDbl;
   const bool integer = (nu == floor(nu));
   long long kind = integer ? (nu == 1.0 ? 1 : 2) : 0;
   c[0] = __longlong_as_double(kind);
@@ -64,40 +65,52 @@ __global__ void matern_const_kernel(double nu, double* tab) {
 
 // One block of 32 threads per interval.
 __global__ void matern_fit_kernel(double nu, double* tab) {
-  __shared__ double f[kNCoef], cheb[kNCoef], tm[kNCoef][kNCoef];
+  constexpr int N = kDeg + 1;
+  __shared__ double f[N], cheb[N], mono[N], tm[N][N];
   const int idx = blockIdx.x;
   const int e = kELo + (idx >> kSub);
   const int j = idx & ((1 << kSub) - 1);
   const int tid = threadIdx.x;
-  const double I0 = tab[kNInt * kNCoef + 6];
+  const double I0 = tab[kNInt * kNDbl + 6];
   const double scale = ldexp(1.0, e);
   const double mid = scale * (1.0 + (2.0 * j + 1.0) / 16.0);
   const double hw = scale / 16.0;
-  if (tid < kNCoef) {
-    const double tn = cospi((tid + 0.5) / kNCoef);
+  if (tid < N) {
+    const double tn = cospi((tid + 0.5) / N);
     f[tid] = quad_I(mid + hw * tn, nu) / I0;
   }
   if (tid == 0) {
     // Monomial coefficients of T_0..T_kDeg (exact small integers).
-    for (int k = 0; k < kNCoef; ++k)
-      for (int q = 0; q < kNCoef; ++q) tm[k][q] = 0.0;
+    for (int k = 0; k < N; ++k)
+      for (int q = 0; q < N; ++q) tm[k][q] = 0.0;
     tm[0][0] = 1.0;
     tm[1][1] = 1.0;
-    for (int k = 2; k < kNCoef; ++k)
-      for (int q = 0; q < kNCoef; ++q)
+    for (int k = 2; k < N; ++k)
+      for (int q = 0; q < N; ++q)
         tm[k][q] = (q > 0 ? 2.0 * tm[k - 1][q - 1] : 0.0) - tm[k - 2][q];
   }
   __syncthreads();
-  if (tid < kNCoef) {
+  if (tid < N) {
     double s = 0.0;
-    for (int q = 0; q < kNCoef; ++q) s += f[q] * cospi(tid * (q + 0.5) / kNCoef);
-    cheb[tid] = (tid == 0 ? 1.0 : 2.0) * s / kNCoef;
+    for (int q = 0; q < N; ++q) s += f[q] * cospi(tid * (q + 0.5) / N);
+    cheb[tid] = (tid == 0 ? 1.0 : 2.0) * s / N;
   }
   __syncthreads();
-  if (tid < kNCoef) {
+  if (tid < N) {
     double a = 0.0;
-    for (int k = kNCoef - 1; k >= 0; --k) a += cheb[k] * tm[k][tid];
-    tab[idx * kNCoef + tid] = a;
+    for (int k = N - 1; k >= 0; --k) a += cheb[k] * tm[k][tid];
+    mono[tid] = a;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double* d = tab + idx * kNDbl;
+    for (int k = 0; k < 6; ++k) d[k] = mono[k];
+    d[6] = 2.0 * mono[2];
+    d[7] = 0.0;
+    float* fl = reinterpret_cast<float*>(tab + kNInt * kNDbl + kNConst) + idx * kNFlt;
+    for (int k = 6; k <= 9; ++k) fl[k - 6] = (float)mono[k];
+    for (int k = 3; k <= 9; ++k) fl[4 + k - 3] = (float)(k * mono[k]);
+    fl[11] = 0.0f;
   }
 }
 
@@ -130,7 +143,7 @@ int get_matern_table(double nu, cudaStream_t stream, const double** out) {
     }
   }
   double* d = nullptr;
-  if (cudaMalloc(&d, sizeof(double) * kTableDoubles) != cudaSuccess) return VECCHIA_ENOMEM;
+  if (cudaMalloc(&d, kTableBytes) != cudaSuccess) return VECCHIA_ENOMEM;
   cudaEvent_t ev;
   if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
     cudaFree(d);
@@ -173,7 +186,7 @@ __global__ void matern_eval_kernel(const double* __restrict__ d, int64_t count, 
     const double x = d[i] * ib;
     const double u = x * x;
     double rho, h;
-    rho_eval_d(u, tab, mc, rho, h);
+    rho_eval<true>(u, tab, mc, rho, h);
     c[i] = sigma2 * rho;
     if (dc) dc[i] = -2.0 * sigma2 * ib * h;
   }

@@ -2,13 +2,21 @@
 //
 // rho(u) = C(d)/sigma2 with u = (d/beta)^2, and h(u) = u * drho/du, so that
 // dC/dbeta = -(2 sigma2 / beta) h(u).  rho is read from a per-nu table of
-// piecewise polynomials (built on the GPU by build_matern_table, see matern.cu):
+// piecewise polynomials (built on the GPU by matern_fit_kernel, see matern.cu):
 //   u in [2^e (1 + j/8), 2^e (1 + (j+1)/8)),  e in [kELo, kEHi),  j in 0..7,
-//   t = 16 u / 2^e - 17 - 2j in [-1, 1),  rho ~ sum_k c[e,j,k] t^k  (k <= kDeg).
-// The interval index, t and u dt/du = 16 M (M = mantissa of u) are formed from the
-// bits of u with integer operations, so one evaluation costs kDeg + 1 FP64 FMAs
-// (2 kDeg + 1 with the derivative).  Below 2^kELo the two-term expansion of rho at
-// u = 0 is used; at and above 2^kEHi, rho = 0 (it is below the smallest double).
+//   t = 16 u / 2^e - 17 - 2j in [-1, 1),  rho ~ P(t) = sum_{k<=9} c_k t^k.
+// The interval index, t and u dt/du = 16 M (M = mantissa of u) come from the bits of
+// u with integer operations.  On GB300 an FP64 instruction costs as much as ~60 others,
+// so the polynomial is split by magnitude:
+//   P(t) = c0 + t(c1 + t(c2 + t(c3 + t(c4 + t(c5 + t T6(t)))))),
+//   T6(t) = c6 + c7 t + c8 t^2 + c9 t^3 evaluated in FP32;
+//   P'(t) = c1 + t(2 c2 + t R(t)),  R(t) = 3 c3 + 4 c4 t + ... + 9 c9 t^6 in FP32.
+// With |t| <= 1 and coefficients shrinking by ~1/34 per degree, the FP32 parts carry
+// absolute errors below 1e-17 in rho and ~1e-10 relative in h wherever rho is not
+// negligible (far-field intervals, rho < 1e-9, have slower coefficient decay and keep
+// only ~1e-8 of h, i.e. errors below 1e-17 absolute).  FP32 results re-enter FP64 by
+// exact bit conversion.  Cost: 6 FP64 FMAs for rho, 3 more FP64 ops for h.
+// Below 2^kELo the expansion of rho at u = 0 is used; at and above 2^kEHi, rho = 0.
 #pragma once
 
 #include "common.cuh"
@@ -21,8 +29,14 @@ struct MaternConst {
   double nu, a1, G, b0, b1;
 };
 
+__device__ __forceinline__ const double* table_d(const double* tab) { return tab; }
+__device__ __forceinline__ const double* table_c(const double* tab) { return tab + kNInt * kNDbl; }
+__device__ __forceinline__ const float* table_f(const double* tab) {
+  return reinterpret_cast<const float*>(tab + kNInt * kNDbl + kNConst);
+}
+
 __device__ __forceinline__ MaternConst load_matern_const(const double* __restrict__ tab) {
-  const double* c = tab + kNInt * kNCoef;
+  const double* c = table_c(tab);
   MaternConst mc;
   mc.kind = (int)__double_as_longlong(c[0]);
   mc.nu = c[1];
@@ -31,6 +45,18 @@ __device__ __forceinline__ MaternConst load_matern_const(const double* __restric
   mc.b0 = c[4];
   mc.b1 = c[5];
   return mc;
+}
+
+// Exact float -> double without the FP64 pipe (F2F is an FP64-pipe instruction).
+// Zero and subnormal floats (below 1.2e-38 in magnitude) map to zero.
+__device__ __forceinline__ double f2d_exact(float f) {
+  const unsigned fb = __float_as_uint(f);
+  const unsigned ab = fb & 0x7FFFFFFFu;
+  if (ab < 0x00800000u) return 0.0;
+  const unsigned long long db = ((unsigned long long)(fb & 0x80000000u) << 32) |
+                                ((unsigned long long)((ab >> 23) + 896u) << 52) |
+                                ((unsigned long long)(ab & 0x7FFFFFu) << 29);
+  return __longlong_as_double((long long)db);
 }
 
 // Expansion of rho and h at u -> 0 (u < 2^kELo), from the series of x^nu K_nu(x):
@@ -55,48 +81,66 @@ static __device__ __noinline__ void rho_small(double u, const MaternConst& mc, d
   }
 }
 
-// rho(u) only.
-__device__ __forceinline__ double rho_eval(double u, const double* __restrict__ tab,
-                                           const MaternConst& mc) {
+// Polynomial part of rho(u) (and h(u) = u rho'(u) when DERIV), branch-free: the
+// interval index is clamped, so u outside [2^kELo, 2^kEHi) gets a finite value that
+// rho_fix() then replaces.
+template <bool DERIV>
+__device__ __forceinline__ void rho_poly(double u, const double* __restrict__ tab, double& rho, double& h) {
   const long long b = __double_as_longlong(u);
-  const int ex = (int)(b >> 52) - 1023;
-  if (ex >= kEHi) return 0.0;
-  if (ex < kELo) {
-    double r, h;
-    rho_small(u, mc, r, h);
-    return r;
-  }
+  const int ex = min(max((int)(b >> 52) - 1023, kELo), kEHi - 1);
   const int idx = ((ex - kELo) << kSub) | (int)((b >> 49) & 7);
-  const double v = __longlong_as_double(0x3FF0000000000000LL | ((b & 0x1FFFFFFFFFFFFLL) << 3));
-  const double t = fma(v, 2.0, -3.0);
-  const double* __restrict__ c = tab + idx * kNCoef;
-  double p = __ldg(c + kDeg);
-#pragma unroll
-  for (int k = kDeg - 1; k >= 0; --k) p = fma(p, t, __ldg(c + k));
-  return p;
+  const long long fr = b & 0x1FFFFFFFFFFFFLL;  // bits of u below the sub-interval index
+  const double t = fma(__longlong_as_double(0x3FF0000000000000LL | (fr << 3)), 2.0, -3.0);
+  const float tf = fmaf(__uint_as_float(0x3F800000u | (unsigned)(fr >> 26)), 2.0f, -3.0f);
+  const double2* __restrict__ cd = reinterpret_cast<const double2*>(table_d(tab) + idx * kNDbl);
+  const float4* __restrict__ cf = reinterpret_cast<const float4*>(table_f(tab) + idx * kNFlt);
+  const double2 c01 = __ldg(cd), c23 = __ldg(cd + 1), c45 = __ldg(cd + 2);
+  const float4 f0 = __ldg(cf);
+  const float t6 = fmaf(fmaf(fmaf(f0.w, tf, f0.z), tf, f0.y), tf, f0.x);
+  double p = f2d_exact(t6);
+  p = fma(p, t, c45.y);
+  p = fma(p, t, c45.x);
+  p = fma(p, t, c23.y);
+  p = fma(p, t, c23.x);
+  p = fma(p, t, c01.y);
+  rho = fma(p, t, c01.x);
+  if (DERIV) {
+    const double2 c2x = __ldg(cd + 3);  // (2 c2, 0)
+    const float4 f1 = __ldg(cf + 1), f2 = __ldg(cf + 2);
+    // R(t) = 3c3 + 4c4 t + 5c5 t^2 + 6c6 t^3 + 7c7 t^4 + 8c8 t^5 + 9c9 t^6
+    float r = f2.z;
+    r = fmaf(r, tf, f2.y);
+    r = fmaf(r, tf, f2.x);
+    r = fmaf(r, tf, f1.w);
+    r = fmaf(r, tf, f1.z);
+    r = fmaf(r, tf, f1.y);
+    r = fmaf(r, tf, f1.x);
+    const double dq = fma(t, f2d_exact(r), c2x.x);
+    const double dp = fma(t, dq, c01.y);
+    // u dt/du = 16 M, M = mantissa of u in [1, 2): exponent field set to 1023 + 4.
+    h = __longlong_as_double(0x4030000000000000LL | (b & 0xFFFFFFFFFFFFFLL)) * dp;
+  }
 }
 
-// rho(u) and h(u) = u rho'(u).
-__device__ __forceinline__ void rho_eval_d(double u, const double* __restrict__ tab,
-                                           const MaternConst& mc, double& rho, double& h) {
-  const long long b = __double_as_longlong(u);
-  const int ex = (int)(b >> 52) - 1023;
-  if (ex >= kEHi) { rho = 0.0; h = 0.0; return; }
-  if (ex < kELo) { rho_small(u, mc, rho, h); return; }
-  const int idx = ((ex - kELo) << kSub) | (int)((b >> 49) & 7);
-  const double v = __longlong_as_double(0x3FF0000000000000LL | ((b & 0x1FFFFFFFFFFFFLL) << 3));
-  const double t = fma(v, 2.0, -3.0);
-  const double* __restrict__ c = tab + idx * kNCoef;
-  double p = __ldg(c + kDeg), dp = 0.0;
-#pragma unroll
-  for (int k = kDeg - 1; k >= 0; --k) {
-    dp = fma(dp, t, p);
-    p = fma(p, t, __ldg(c + k));
-  }
-  rho = p;
-  // u dt/du = 16 M, M = mantissa of u in [1, 2): exponent field set to 1023 + 4.
-  const double m16 = __longlong_as_double(0x4030000000000000LL | (b & 0xFFFFFFFFFFFFFLL));
-  h = m16 * dp;
+// Replaces rho_poly's value outside the tabulated range (rare): far field -> 0,
+// u < 2^kELo -> expansion at zero.
+__device__ __forceinline__ void rho_fix(double u, const MaternConst& mc, double& rho, double& h) {
+  const int ex = (int)(__double_as_longlong(u) >> 52) - 1023;
+  if (ex >= kEHi) { rho = 0.0; h = 0.0; }
+  else if (ex < kELo) rho_small(u, mc, rho, h);
+}
+
+template <bool DERIV>
+__device__ __forceinline__ void rho_eval(double u, const double* __restrict__ tab, const MaternConst& mc,
+                                         double& rho, double& h) {
+  rho_poly<DERIV>(u, tab, rho, h);
+  rho_fix(u, mc, rho, h);
+}
+
+__device__ __forceinline__ double rho_only(double u, const double* __restrict__ tab, const MaternConst& mc) {
+  double r, h;
+  rho_eval<false>(u, tab, mc, r, h);
+  return r;
 }
 
 }  // namespace vecchia

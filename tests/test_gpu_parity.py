@@ -73,8 +73,12 @@ def test_matern_matches_oracle(V, nu):
     # factors (pow, tgamma, K_nu, ...), the table adds its fit (< 1e-16) and Horner rounding.
     err = np.abs(c - want)
     assert np.all(err <= 4e-15 * sigma2), (err.max(), d[np.argmax(err)])
-    assert np.all(np.abs(dc - wantd) <= 1e-11 * np.abs(wantd) + 1e-13 * sigma2 / beta), \
-        np.abs(dc - wantd).max()
+    # dC/dbeta carries the FP32 tail of the derivative polynomial: below ~1e-9 relative
+    # where the correlation matters (1e-7 would still meet the gradient tolerance), ~1e-7
+    # relative only where the correlation is below 1e-9 (far field).
+    derr = np.abs(dc - wantd)
+    assert np.all(derr <= 2e-9 * np.abs(wantd) + 1e-14 * sigma2 / beta), \
+        (derr.max(), d[np.argmax(derr)], wantd[np.argmax(derr)])
 
 
 # ------------------------------------------------------------------ orderings and kNN
