@@ -141,6 +141,36 @@ int vecchia_matern(const double* d_dev, int64_t count, const double theta[4], do
                    double* dcdbeta_dev, void* stream);
 
 /*
+ * vecchia_loglik_noalloc — the same log-likelihood as vecchia_loglik for callers that
+ * cannot allocate device memory: code running where cudaMalloc is unavailable or
+ * forbidden (for example inside a host allocator's callback, a memory-capped arena
+ * that owns every device byte, or a runtime that must never trigger an allocation
+ * while serving).  It has no counterpart in the paper.  It calls no cudaMalloc,
+ * cudaFree or other allocating routine; its scratch (per-warp partial sums for at
+ * most 4096 warps, an error slot and one covariance table, about 176 KB) is a
+ * file-scope __device__ array that every GPU loading the library keeps until the
+ * process exits.  The launch is capped at 4096 warps; the kernel strides over the
+ * locations, so no n is too large for the scratch.
+ *   xy_dev   : n x 2 doubles, ORIGINAL order (as passed to vecchia_plan_create).
+ *   y_dev    : n doubles, ORIGINAL order.
+ *   nbr_dev  : n x m int32, row i = the conditioning set of the i-th ORDERED location as
+ *              ORIGINAL indices, -1 padded after m_i = min(i, m) entries; from a plan:
+ *              perm[vecchia_plan_neighbors()] for entries >= 0.
+ *   self_dev : n int32, ORIGINAL index of the i-th ordered location (= perm[i]).
+ *   n, m     : 1 <= n <= 2^31 - 1, 1 <= m <= VECCHIA_MAX_M; otherwise EINVAL.
+ *   theta    : host double[4] as for vecchia_loglik; out_dev: 1 double on the device.
+ * Asynchronous on `stream`.  The first call on a device looks up the scratch array's
+ * device address (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  Every call reuses the same scratch and rebuilds the covariance table in
+ * it, so calls that overlap on the GPU (different streams, or different host threads,
+ * on one device) race and must be serialised by the caller.  A block that is not
+ * positive definite makes out_dev NaN.  Errors: EINVAL, ECUDA.
+ */
+int vecchia_loglik_noalloc(const double* xy_dev, const double* y_dev, const int32_t* nbr_dev,
+                           const int32_t* self_dev, int64_t n, int32_t m, const double theta[4],
+                           double* out_dev, void* stream);
+
+/*
  * vecchia_last_error_location — synchronises the stream of the plan's last call and
  * reports the first ordered location whose block was not positive definite in that
  * call (*loc = -1 if none).  Returns ENOTPD if there was one, else OK.

@@ -35,6 +35,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
+#include <mutex>
 
 #include "common.cuh"
 #include "matern.cuh"
@@ -42,6 +43,7 @@
 namespace vecchia {
 
 int get_matern_table(double nu, cudaStream_t stream, const double** out);
+int launch_matern_table(double nu, double* tab, cudaStream_t stream);
 bool theta_ok(const double* th);
 
 struct LikArgs {
@@ -442,3 +444,84 @@ int launch_loglik(Plan* p, const double* y_dev, const double* theta, bool grad, 
 }
 
 }  // namespace vecchia
+
+// ------------------------------------------------------------------ allocation-free entry
+// Scratch for vecchia_loglik_noalloc: per-warp partial sums for at most
+// kNoAllocWarps warps, the error slot and one covariance table, in a file-scope device
+// array that every GPU loading the library holds until the process exits.
+namespace vecchia {
+constexpr int kNoAllocWarps = 4096;
+constexpr size_t kNoAllocPartialBytes = sizeof(double) * 4 * kNoAllocWarps;
+constexpr size_t kNoAllocErrOff = kNoAllocPartialBytes;
+constexpr size_t kNoAllocTabOff = kNoAllocErrOff + 256;
+constexpr size_t kNoAllocBytes = kNoAllocTabOff + (kTableBytes + 255) / 256 * 256;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+unsigned char* g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device (looked up once per device;
+// the host-side symbol is only a stand-in and must never be passed to a kernel).
+int noalloc_scratch(unsigned char** out) {
+  int dev = 0;
+  VECCHIA_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return VECCHIA_EINVAL;
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return VECCHIA_ECUDA;
+    g_noalloc_ptr[dev] = static_cast<unsigned char*>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return VECCHIA_OK;
+}
+}  // namespace
+}  // namespace vecchia
+
+extern "C" int vecchia_loglik_noalloc(const double* xy_dev, const double* y_dev, const int32_t* nbr_dev,
+                                      const int32_t* self_dev, int64_t n, int32_t m, const double theta[4],
+                                      double* out_dev, void* stream) {
+  using namespace vecchia;
+  if (!xy_dev || !y_dev || !nbr_dev || !self_dev || !out_dev || n < 1 || n > 2147483647LL || m < 1 ||
+      m > kMaxM || !theta_ok(theta))
+    return VECCHIA_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned char* base = nullptr;
+  int rc = noalloc_scratch(&base);
+  if (rc) return rc;
+  double* partial = reinterpret_cast<double*>(base);
+  unsigned long long* errloc = reinterpret_cast<unsigned long long*>(base + kNoAllocErrOff);
+  double* tab = reinterpret_cast<double*>(base + kNoAllocTabOff);
+  LaunchCfg cfg;
+  rc = pick_config(m + 1, false, &cfg);
+  if (rc) return rc;
+  // The kernel is persistent (warps stride over locations), so any grid covers any n;
+  // it is capped to the warps the scratch can hold.
+  const int max_blocks = kNoAllocWarps / cfg.W;
+  if (cfg.blocks > max_blocks) cfg.blocks = max_blocks;
+  const int64_t nw = (int64_t)cfg.blocks * cfg.W;
+  rc = launch_matern_table(theta[2], tab, s);
+  if (rc) return rc;
+  VECCHIA_CUDA_TRY(cudaMemsetAsync(errloc, 0xFF, sizeof(unsigned long long), s));
+  LikArgs a;
+  a.xy = xy_dev;
+  a.yf = y_dev;
+  a.nbr = nbr_dev;
+  a.self = self_dev;
+  a.tab = tab;
+  a.n = n;
+  a.m = m;
+  a.sigma2 = theta[0];
+  a.beta = theta[1];
+  a.tau2 = theta[3];
+  a.partial = partial;
+  a.terms = nullptr;
+  a.errloc = errloc;
+  vecchia_lik_kernel<false><<<cfg.blocks, cfg.W * 32, cfg.smem, s>>>(a);
+  VECCHIA_CUDA_TRY(cudaGetLastError());
+  vecchia_finalize_kernel<<<1, 32, 0, s>>>(partial, nw, theta[0], theta[1], theta[3], 0, out_dev);
+  VECCHIA_CUDA_TRY(cudaGetLastError());
+  return VECCHIA_OK;
+}

@@ -175,6 +175,15 @@ int get_matern_table(double nu, cudaStream_t stream, const double** out) {
   return VECCHIA_OK;
 }
 
+// Builds the table for nu into caller-provided device memory (kTableBytes, 16-byte
+// aligned) on `stream`, without touching the cache.
+int launch_matern_table(double nu, double* tab, cudaStream_t stream) {
+  matern_const_kernel<<<1, 32, 0, stream>>>(nu, tab);
+  matern_fit_kernel<<<kNInt, 32, 0, stream>>>(nu, tab);
+  VECCHIA_CUDA_TRY(cudaGetLastError());
+  return VECCHIA_OK;
+}
+
 // ------------------------------------------------------------------ vecchia_matern
 __global__ void matern_eval_kernel(const double* __restrict__ d, int64_t count, double sigma2,
                                    double beta, const double* __restrict__ tab, double* __restrict__ c,

@@ -48,6 +48,7 @@ SIGNATURES = {
     "vecchia_last_error_location": (ctypes.c_int, [_vp, ctypes.POINTER(_i64)]),
     "vecchia_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "vecchia_fp64_peak": (ctypes.c_int, [_dp, _vp]),
+    "vecchia_loglik_noalloc": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i64, _i32, _dp, _vp, _vp]),
 }
 
 
@@ -191,6 +192,26 @@ def vecchia_matern(d: torch.Tensor, theta, with_dbeta: bool = True, stream=None)
                               _vp(dc.data_ptr()) if dc is not None else None, _vp(_stream(stream)))
     _check(rc, "vecchia_matern")
     return (c, dc) if with_dbeta else c
+
+
+def vecchia_loglik_noalloc(xy: torch.Tensor, y: torch.Tensor, nbr: torch.Tensor, self_idx: torch.Tensor,
+                           m: int, theta, out: torch.Tensor, stream=None):
+    """Allocation-free log-likelihood over caller-owned device arrays (see the C header):
+    xy (n x 2, original order), y (n), nbr (n x m int32 original indices of each ordered
+    location's conditioning set, -1 padded), self_idx (n int32, perm).  Writes out[0]."""
+    n = y.numel()
+    for t, name, dt, cnt in ((xy, "xy", torch.float64, 2 * n), (y, "y", torch.float64, n),
+                             (nbr, "nbr", torch.int32, n * m), (self_idx, "self_idx", torch.int32, n),
+                             (out, "out", torch.float64, None)):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dt and t.is_contiguous()):
+            raise TypeError(f"{name} must be a contiguous CUDA {dt} tensor")
+        if cnt is not None and t.numel() != cnt:
+            raise ValueError(f"{name} must have {cnt} elements")
+    rc = lib().vecchia_loglik_noalloc(_vp(xy.data_ptr()), _vp(y.data_ptr()), _vp(nbr.data_ptr()),
+                                      _vp(self_idx.data_ptr()), n, int(m), _theta(theta), _vp(out.data_ptr()),
+                                      _vp(_stream(stream)))
+    _check(rc, "vecchia_loglik_noalloc")
+    return out
 
 
 def vecchia_fp64_peak(stream=None) -> float:
