@@ -141,6 +141,42 @@ int vecchia_matern(const double* d_dev, int64_t count, const double theta[4], do
                    double* dcdbeta_dev, void* stream);
 
 /*
+ * vecchia_batched_prepare — builds the covariance tables the batched call may use, one per
+ * smoothness value nus[0..nnu-1] (each > 0 and finite, 1 <= nnu <= 8), on the current
+ * device, replacing the previously prepared set.  Synchronises `stream` before and after
+ * (tables in use by earlier batched launches on that stream are not overwritten early).
+ * Must precede vecchia_loglik_batched and any graph capture of it.  Errors: EINVAL,
+ * ENOMEM, ECUDA.
+ */
+int vecchia_batched_prepare(const double* nus, int32_t nnu, void* stream);
+
+/*
+ * vecchia_loglik_batched — many (field, theta) evaluations in one persistent launch (not
+ * in the paper, which batches only over the locations of one field).
+ *   plans      : nfields plan handles (host array); fields may differ in n and m (at most
+ *                four distinct m per call).
+ *   y_devs     : nfields device pointers (host array), field f's n values in the ORIGINAL
+ *                order of plans[f].
+ *   thetas_dev : nfields x ntheta x 4 doubles on the DEVICE, row-major; each theta's nu
+ *                must be one of the values given to vecchia_batched_prepare (compared bit
+ *                for bit).
+ *   want_grad  : 0 -> out_dev has 1 double per (field, theta): l; else 4:
+ *                {l, dl/dsigma2, dl/dbeta, dl/dtau2}.
+ *   out_dev    : nfields x ntheta x (1|4) doubles on the device.
+ * Asynchronous on `stream`.  The first call for a given (plans, y_devs, ntheta, want_grad)
+ * lays out the work and allocates for it (it must not be made during stream capture:
+ * EINVAL); later calls with the same arguments reuse that layout, allocate nothing and
+ * may be captured in a CUDA graph and replayed with new values in thetas_dev.  A theta
+ * whose nu was not prepared, an invalid theta or a block that is not positive definite
+ * makes that (field, theta)'s outputs NaN.  Destroying a plan drops the layouts that use
+ * it.  Errors: EINVAL (arguments, nothing prepared, more than four distinct m), ENOMEM,
+ * ECUDA.
+ */
+int vecchia_loglik_batched(const vecchia_plan_t* plans, const double* const* y_devs, int32_t nfields,
+                           const double* thetas_dev, int32_t ntheta, int want_grad, double* out_dev,
+                           void* stream);
+
+/*
  * vecchia_loglik_noalloc — the same log-likelihood as vecchia_loglik for callers that
  * cannot allocate device memory: code running where cudaMalloc is unavailable or
  * forbidden (for example inside a host allocator's callback, a memory-capped arena

@@ -1,0 +1,358 @@
+// One ordered location's Vecchia term, computed by one warp in shared memory
+// (Sec. V-B, Algorithm 1), shared by the single-field and the batched kernels.
+//
+// For location i with conditioning set J (m_i = min(i, m) real neighbours, the rest
+// identity padding) the warp builds the bordered (K+1) x (K+1) lower triangle, K = m + 1,
+//
+//        rows 0..m-1 : neighbours J (pads: identity rows)       | border row K:
+//        row  m      : the location itself                        |   y_B
+//     M = [ R_B + gamma I      .  ]    R_B = correlation block, gamma = tau2/sigma2
+//         [ y_B^T              0  ]
+//
+// and runs K-1 steps of an in-place L D L^T elimination over the neighbour columns.
+// What remains in the trailing 2x2 corner is exactly Algorithm 1's correction:
+//   M[m][m] = s_i / sigma2   (conditional variance, lines 20 and 23),
+//   M[K][m] = y_i - mu_i      (conditional residual, lines 16-19 and 22),
+// so the batched POTRF, the two TRSVs and the two dot products of Algorithm 1 become
+// one elimination of the bordered block, and the univariate term (line 24)
+//   l_i = -1/2 (y_i - mu_i)^2 / s_i - 1/2 log s_i - 1/2 log 2 pi.
+//
+// Storage: the triangle is packed column by column from the last column (K) to the
+// first, so the columns still to be updated at step j form a prefix [0, off(j)),
+// off(c) = (K-c)(K-c+1)/2.  Every FP64 instruction is issued with as many active lanes
+// as the trailing prefix allows; pivots use one reciprocal (no square root).
+//
+// Adjoint (not in the paper).  With w = Sigma_JJ^{-1} v, alpha = Sigma_JJ^{-1} y_J,
+// r = y_i - mu_i and s = s_i, write w^ = [-w; 1], a^ = [alpha; 0] and
+//   g = (r/s) a^ + 1/2 (r^2/s^2 - 1/s) w^.
+// Then dl_i/dtheta_p = w^T (dSigma_B/dtheta_p) g, hence
+//   dl_i/dtau2   = w^T g,
+//   dl_i/dsigma2 = (1/2 (r^2/s - 1) - tau2 w^T g) / sigma2   (uses Sigma_B w^ = s e_i),
+//   dl_i/dbeta   = -(2 sigma2/beta) sum_{p>q} h(u_pq) (w^_p g_q + w^_q g_p),
+// where h = u rho'(u).  w and alpha come from two backward solves with the unit
+// factor already in shared memory (rows m and K of L are L_J^{-1}-scaled v and y_J).
+#pragma once
+
+#include "common.cuh"
+#include "matern.cuh"
+
+namespace vecchia {
+
+__host__ __device__ __forceinline__ int tri_off(int K, int c) { return (K - c) * (K - c + 1) / 2; }
+
+__host__ __device__ __forceinline__ int align_up(int x, int a) { return (x + a - 1) / a * a; }
+
+// Schedule sizes for block size K (= m + 1): NT packed slots, NP correlation pairs.
+struct SchedSize {
+  int NT, NP, sched_bytes, pairs_bytes;
+  __host__ __device__ explicit SchedSize(int K) {
+    NT = (K + 1) * (K + 2) / 2;
+    NP = K * (K - 1) / 2;
+    sched_bytes = align_up(NT * 2, 16);
+    pairs_bytes = align_up(NP * 4, 16);
+  }
+};
+
+// Per-warp shared-memory area for blocks up to size K.
+struct WarpArea {
+  double *A, *X, *Y, *YV, *TV, *H, *WH, *GV;
+  __host__ __device__ static int doubles(int K, bool grad) {
+    const SchedSize S(K);
+    int d = align_up(S.NT, 2) + 4 * align_up(K + 1, 2);
+    if (grad) d += align_up(S.NP, 2) + 2 * align_up(K + 1, 2);
+    return d;
+  }
+  __device__ WarpArea(double* base, int K) {
+    const SchedSize S(K);
+    A = base;
+    X = A + align_up(S.NT, 2);
+    Y = X + align_up(K + 1, 2);
+    YV = Y + align_up(K + 1, 2);
+    TV = YV + align_up(K + 1, 2);
+    H = TV + align_up(K + 1, 2);
+    WH = H + align_up(S.NP, 2);
+    GV = WH + align_up(K + 1, 2);
+  }
+};
+
+// Element schedules for block size K: sched[e] = (row, col) of packed slot e;
+// pairs[q] = (row, col, slot) of the q-th strictly-lower pair of the K x K block.
+__device__ __forceinline__ void build_schedules(int K, uint16_t* sched, uint32_t* pairs) {
+  for (int c = threadIdx.x; c <= K; c += blockDim.x) {
+    const int o = tri_off(K, c);
+    for (int r = c; r <= K; ++r) sched[o + r - c] = (uint16_t)(r | (c << 8));
+    if (c < K - 1) {
+      const int base = (K - 1 - c) * (K - 2 - c) / 2;
+      for (int r = c + 1; r <= K - 1; ++r)
+        pairs[base + r - c - 1] = (uint32_t)r | ((uint32_t)c << 8) | ((uint32_t)(o + r - c) << 16);
+    }
+  }
+}
+
+// theta-dependent constants of one evaluation.
+struct ThetaConst {
+  double sigma2, inv_beta, gamma1, inv_sigma2, tau2;
+  __device__ void set(double s2, double beta, double t2) {
+    sigma2 = s2;
+    inv_beta = 1.0 / beta;
+    gamma1 = 1.0 + t2 / s2;
+    inv_sigma2 = 1.0 / s2;
+    tau2 = t2;
+  }
+};
+
+// Running sums of a warp: sum l_i (identical on all lanes), sum 1/2 (r^2/s - 1), and the
+// per-lane partial sums of the beta pair sums and of w^T g.
+struct Accum {
+  Neumaier L;
+  double S = 0.0, B = 0.0, T = 0.0;
+};
+
+// Field description: device arrays of one field and its plan.
+struct FieldView {
+  const double2* __restrict__ xy;   // n, original order
+  const double* __restrict__ yf;    // n, original order
+  const int32_t* __restrict__ nbr;  // n x m original indices
+  const int32_t* __restrict__ self; // n
+  int64_t n;
+  int m;
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Processes ordered location i of field F.  terms (optional) receives l_i, or
+// {l_i, dl_i/dsigma2, dl_i/dbeta, dl_i/dtau2} when GRAD.  Returns false when the block
+// was not positive definite (the term is then NaN and i is recorded in errloc).
+template <bool GRAD>
+__device__ __forceinline__ bool process_location(int64_t i, const FieldView& F, const SchedSize& S,
+                                                 const uint16_t* __restrict__ sched,
+                                                 const uint32_t* __restrict__ pairs, const WarpArea& W,
+                                                 const double* __restrict__ tab, const MaternConst& mc,
+                                                 const ThetaConst& tc, Accum& acc, double* terms,
+                                                 unsigned long long* errloc, int lane) {
+  const int m = F.m;
+  const int K = m + 1;
+  double* __restrict__ A = W.A;
+  double* __restrict__ X = W.X;
+  double* __restrict__ Y = W.Y;
+  double* __restrict__ YV = W.YV;
+  double* __restrict__ TV = W.TV;
+  const int mi = i < m ? (int)i : m;
+  const int32_t* __restrict__ row = F.nbr + i * m;
+  const int js = F.self[i];
+  const double2 ps = F.xy[js];
+  // ---- gather: centred, 1/beta-scaled coordinates and data of the block rows
+  for (int p = lane; p < m; p += 32) {
+    double xv = 0.0, yv = 0.0, fv = 0.0;
+    if (p < mi) {
+      const int j = row[p];
+      const double2 q = F.xy[j];
+      xv = (q.x - ps.x) * tc.inv_beta;
+      yv = (q.y - ps.y) * tc.inv_beta;
+      fv = F.yf[j];
+    }
+    X[p] = xv;
+    Y[p] = yv;
+    YV[p] = fv;
+  }
+  if (lane == 0) {
+    X[m] = 0.0;
+    Y[m] = 0.0;
+    YV[m] = F.yf[js];
+  }
+  __syncwarp();
+  // ---- assemble: diagonal, data border, then the correlation pairs
+  for (int c = lane; c < K; c += 32) {
+    const int o = tri_off(K, c);
+    A[o] = (c >= mi && c < m) ? 1.0 : tc.gamma1;
+    A[o + K - c] = YV[c];
+  }
+  if (lane == 0) A[0] = 0.0;
+  // Two pairs per lane per iteration so one pair's loads overlap the other's FMAs.
+  for (int q0 = lane; q0 < S.NP; q0 += 64) {
+    const int q1 = q0 + 32;
+    const bool has1 = q1 < S.NP;
+    const uint32_t w0 = pairs[q0];
+    const uint32_t w1 = has1 ? pairs[q1] : w0;
+    const int r0 = w0 & 0xFF, c0 = (w0 >> 8) & 0xFF;
+    const int r1 = w1 & 0xFF, c1 = (w1 >> 8) & 0xFF;
+    const bool v0 = c0 < mi && (r0 < mi || r0 == m);
+    const bool v1 = has1 && c1 < mi && (r1 < mi || r1 == m);
+    const double dx0 = X[r0] - X[c0], dy0 = Y[r0] - Y[c0];
+    const double dx1 = X[r1] - X[c1], dy1 = Y[r1] - Y[c1];
+    const double u0 = fma(dx0, dx0, dy0 * dy0), u1 = fma(dx1, dx1, dy1 * dy1);
+    double val0, hv0 = 0.0, val1, hv1 = 0.0;
+    rho_poly<GRAD>(u0, tab, val0, hv0);
+    rho_poly<GRAD>(u1, tab, val1, hv1);
+    rho_fix(u0, mc, val0, hv0);
+    rho_fix(u1, mc, val1, hv1);
+    if (!v0) { val0 = 0.0; hv0 = 0.0; }
+    if (!v1) { val1 = 0.0; hv1 = 0.0; }
+    A[w0 >> 16] = val0;
+    if (GRAD) W.H[q0] = hv0;
+    if (has1) {
+      A[w1 >> 16] = val1;
+      if (GRAD) W.H[q1] = hv1;
+    }
+  }
+  __syncwarp();
+  // ---- L D L^T over the neighbour columns
+  bool ok = true;
+  for (int j = 0; j < K - 1; ++j) {
+    const int oj = tri_off(K, j);
+    const double d = A[oj];
+    if (!positive_finite(d)) { ok = false; break; }
+    const double inv = rcp_newton(d);
+    for (int r = j + 1 + lane; r <= K; r += 32) {
+      const double tv = A[oj + r - j];
+      TV[r] = tv;
+      A[oj + r - j] = tv * inv;
+    }
+    __syncwarp();
+    // Trailing update of the prefix [1, oj), four slots per lane per batch: the next
+    // batch's shared-memory loads are issued before this batch's results are stored.
+    const double* Lc = A + oj - j;  // Lc[r] = L[r][j]
+    constexpr int U = 4;
+    double lv[U], tv[U], av[U];
+    int ee[U];
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      ee[k] = 1 + lane + 32 * k;
+      const int ek = ee[k] < oj ? ee[k] : 0;
+      const uint32_t rc = sched[ek];
+      lv[k] = Lc[rc & 0xFF];
+      tv[k] = TV[rc >> 8];
+      av[k] = A[ek];
+    }
+    for (int base = 1 + lane; base < oj; base += 32 * U) {
+      double res[U];
+#pragma unroll
+      for (int k = 0; k < U; ++k) res[k] = fma(-lv[k], tv[k], av[k]);
+      int ne[U];
+#pragma unroll
+      for (int k = 0; k < U; ++k) {
+        ne[k] = base + 32 * (U + k);
+        const int ek = ne[k] < oj ? ne[k] : 0;
+        const uint32_t rc = sched[ek];
+        lv[k] = Lc[rc & 0xFF];
+        tv[k] = TV[rc >> 8];
+        av[k] = A[ek];
+      }
+#pragma unroll
+      for (int k = 0; k < U; ++k) {
+        if (ee[k] < oj) A[ee[k]] = res[k];
+        ee[k] = ne[k];
+      }
+    }
+    __syncwarp();
+  }
+  const double st = A[1];  // s_i / sigma2
+  const double rr = A[2];  // y_i - mu_i
+  if (!ok || !positive_finite(st)) {
+    if (lane == 0) {
+      atomicMin(errloc, (unsigned long long)i);
+      if (terms) {
+        const int tw = GRAD ? 4 : 1;
+        for (int k = 0; k < tw; ++k) terms[k] = __longlong_as_double(0x7FF8000000000000LL);
+      }
+    }
+    acc.L.add(__longlong_as_double(0x7FF8000000000000LL));
+    __syncwarp();
+    return false;
+  }
+  const double s = tc.sigma2 * st;
+  const double inv_s = rcp_newton(s);
+  const double li = -0.5 * rr * rr * inv_s - 0.5 * log(s) - 0.91893853320467274178;
+  acc.L.add(li);
+  if (!GRAD) {
+    if (terms && lane == 0) terms[0] = li;
+    __syncwarp();
+    return true;
+  }
+  // ---- adjoint: w = L_J^{-T} (row m of L), alpha~ = L_J^{-T} (row K of L)
+  double* __restrict__ WH = W.WH;
+  double* __restrict__ GV = W.GV;
+  double w0 = 0.0, w1 = 0.0, b0 = 0.0, b1 = 0.0;
+  const int c0 = lane, c1 = lane + 32;
+  if (c0 < K - 1) { const int o = tri_off(K, c0); w0 = A[o + m - c0]; b0 = A[o + K - c0]; }
+  if (c1 < K - 1) { const int o = tri_off(K, c1); w1 = A[o + m - c1]; b1 = A[o + K - c1]; }
+  for (int c = K - 2; c >= 1; --c) {
+    const int src = c & 31;
+    const double wc = __shfl_sync(0xffffffffu, c >= 32 ? w1 : w0, src);
+    const double bc = __shfl_sync(0xffffffffu, c >= 32 ? b1 : b0, src);
+    if (c0 < c) {
+      const double l = A[tri_off(K, c0) + c - c0];
+      w0 = fma(-l, wc, w0);
+      b0 = fma(-l, bc, b0);
+    }
+    if (c1 < c) {
+      const double l = A[tri_off(K, c1) + c - c1];
+      w1 = fma(-l, wc, w1);
+      b1 = fma(-l, bc, b1);
+    }
+  }
+  const double rs = rr * inv_s;
+  const double cb = 0.5 * (rs * rs - inv_s);
+  const double rsa = rs * tc.inv_sigma2;  // alpha = alpha~ / sigma2
+  double pT = 0.0;
+  if (c0 < K - 1) {
+    const double wh = -w0, gv = fma(rsa, b0, cb * wh);
+    WH[c0] = wh;
+    GV[c0] = gv;
+    pT = fma(wh, gv, pT);
+  }
+  if (c1 < K - 1) {
+    const double wh = -w1, gv = fma(rsa, b1, cb * wh);
+    WH[c1] = wh;
+    GV[c1] = gv;
+    pT = fma(wh, gv, pT);
+  }
+  if (lane == 0) {
+    WH[m] = 1.0;
+    GV[m] = cb;
+    pT += cb;
+  }
+  const double sS = 0.5 * (rr * rs - 1.0);
+  acc.S += sS;
+  __syncwarp();
+  double pB = 0.0;
+  for (int q = lane; q < S.NP; q += 32) {
+    const uint32_t w = pairs[q];
+    const int r = w & 0xFF, c = (w >> 8) & 0xFF;
+    double t = WH[r] * GV[c];
+    t = fma(WH[c], GV[r], t);
+    pB = fma(W.H[q], t, pB);
+  }
+  if (terms) {
+    const double tB = warp_sum(pB), tT = warp_sum(pT);
+    if (lane == 0) {
+      terms[0] = li;
+      terms[1] = (sS - tc.tau2 * tT) * tc.inv_sigma2;
+      terms[2] = -2.0 * tc.sigma2 * tc.inv_beta * tB;
+      terms[3] = tT;
+    }
+  }
+  acc.B += pB;
+  acc.T += pT;
+  __syncwarp();
+  return true;
+}
+
+// Converts a warp's (reduced) sums into the four output slots
+// {l, sum 1/2(r^2/s - 1), sum of beta pair sums, sum w^T g}.
+__device__ __forceinline__ void write_partial(Accum& acc, double* out, int lane) {
+  const double B = warp_sum(acc.B);
+  const double T = warp_sum(acc.T);
+  if (lane == 0) {
+    out[0] = acc.L.value();
+    out[1] = acc.S;
+    out[2] = B;
+    out[3] = T;
+  }
+}
+
+}  // namespace vecchia

@@ -81,6 +81,9 @@ struct Neumaier {
 
 }  // namespace vecchia
 
+// The C ABI's opaque plan handle is a Plan.
+struct vecchia_plan : public vecchia::Plan {};
+
 #define VECCHIA_CUDA_TRY(expr)                        \
   do {                                                \
     cudaError_t _e = (expr);                          \

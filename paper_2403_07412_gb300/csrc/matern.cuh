@@ -11,11 +11,13 @@
 //   P(t) = c0 + t(c1 + t(c2 + t(c3 + t(c4 + t(c5 + t T6(t)))))),
 //   T6(t) = c6 + c7 t + c8 t^2 + c9 t^3 evaluated in FP32;
 //   P'(t) = c1 + t(2 c2 + t R(t)),  R(t) = 3 c3 + 4 c4 t + ... + 9 c9 t^6 in FP32.
-// With |t| <= 1 and coefficients shrinking by ~1/34 per degree, the FP32 parts carry
-// absolute errors below 1e-17 in rho and ~1e-10 relative in h wherever rho is not
-// negligible (far-field intervals, rho < 1e-9, have slower coefficient decay and keep
-// only ~1e-8 of h, i.e. errors below 1e-17 absolute).  FP32 results re-enter FP64 by
-// exact bit conversion.  Cost: 6 FP64 FMAs for rho, 3 more FP64 ops for h.
+// With |t| <= 1 and coefficients shrinking by ~1/34 per degree near the origin (more
+// slowly in the far field, where rho changes by a large factor across an interval), the
+// FP32 part of rho stays below FP64 rounding (measured: no change to the ~1e-16 absolute
+// error of an all-FP64 Horner), and h keeps ~1e-9 relative accuracy where rho > 1e-3 and
+// a few 1e-8 where rho < 1e-6: absolute errors far below 1e-10 of max |h|, which is what
+// the beta-gradient (a sum of h-weighted pair terms) needs.  FP32 results re-enter FP64
+// by exact bit conversion.  Cost: 6 FP64 FMAs for rho, 3 more FP64 ops for h.
 // Below 2^kELo the expansion of rho at u = 0 is used; at and above 2^kEHi, rho = 0.
 #pragma once
 
@@ -59,6 +61,18 @@ __device__ __forceinline__ double f2d_exact(float f) {
   return __longlong_as_double((long long)db);
 }
 
+// t = s 2^-48 for an integer |s| <= 2^48, converted exactly with integer operations
+// (t = 16 u / 2^e - 17 - 2j is this fixed-point value for s = fraction bits - 2^48).
+__device__ __forceinline__ double fixed_to_double_2m48(long long s) {
+  if (s == 0) return 0.0;
+  const unsigned long long sign = s < 0 ? 0x8000000000000000ULL : 0ULL;
+  const unsigned long long a = (unsigned long long)(s < 0 ? -s : s);
+  const int lz = __clzll((long long)a);             // leading one at bit 63 - lz
+  const unsigned long long e = (unsigned long long)(1023 + (63 - lz) - 48);
+  const unsigned long long mant = (a << (lz + 1)) >> 12;
+  return __longlong_as_double((long long)(sign | (e << 52) | mant));
+}
+
 // Expansion of rho and h at u -> 0 (u < 2^kELo), from the series of x^nu K_nu(x):
 //   non-integer nu: rho = 1 + u/(4(1-nu)) - Gamma(1-nu) (u/4)^nu [1/Gamma(1+nu) + (u/4)/Gamma(2+nu)]
 //   nu = 1:          rho = 1 + (u/4)(log(u/4) + 2 gamma_E - 1)
@@ -90,7 +104,7 @@ __device__ __forceinline__ void rho_poly(double u, const double* __restrict__ ta
   const int ex = min(max((int)(b >> 52) - 1023, kELo), kEHi - 1);
   const int idx = ((ex - kELo) << kSub) | (int)((b >> 49) & 7);
   const long long fr = b & 0x1FFFFFFFFFFFFLL;  // bits of u below the sub-interval index
-  const double t = fma(__longlong_as_double(0x3FF0000000000000LL | (fr << 3)), 2.0, -3.0);
+  const double t = fixed_to_double_2m48(fr - (1LL << 48));
   const float tf = fmaf(__uint_as_float(0x3F800000u | (unsigned)(fr >> 26)), 2.0f, -3.0f);
   const double2* __restrict__ cd = reinterpret_cast<const double2*>(table_d(tab) + idx * kNDbl);
   const float4* __restrict__ cf = reinterpret_cast<const float4*>(table_f(tab) + idx * kNFlt);

@@ -381,12 +381,11 @@ static void plan_free(Plan* p) {
 
 int launch_loglik(Plan* p, const double* y_dev, const double* theta, bool grad, double* out_dev,
                   double* terms_dev, cudaStream_t stream);
+void forget_plan_in_batches(const void* plan);
 
 }  // namespace vecchia
 
 using vecchia::Plan;
-
-struct vecchia_plan : public Plan {};
 
 extern "C" {
 
@@ -453,6 +452,7 @@ int vecchia_plan_create(const double* xy_host, int64_t n, int32_t m, int order, 
 void vecchia_plan_destroy(vecchia_plan_t plan) {
   if (!plan) return;
   cudaDeviceSynchronize();
+  vecchia::forget_plan_in_batches(plan);
   vecchia::plan_free(plan);
 }
 

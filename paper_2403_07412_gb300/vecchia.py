@@ -6,7 +6,9 @@ absence is an error: there is no CPU fallback.
 
 The entry points keep the C names: :func:`vecchia_plan_create` (wrapped by
 :class:`Plan`), :func:`vecchia_loglik`, :func:`vecchia_loglik_grad`,
-:func:`vecchia_loglik_terms`, :func:`vecchia_matern`, :func:`vecchia_fp64_peak`;
+:func:`vecchia_loglik_terms`, :func:`vecchia_matern`, :func:`vecchia_fp64_peak`,
+:func:`vecchia_batched_prepare` and :class:`Batch` (vecchia_loglik_batched),
+:func:`vecchia_loglik_noalloc`;
 :class:`VecchiaLogLik` is the ``torch.autograd.Function`` over theta.
 """
 from __future__ import annotations
@@ -49,6 +51,9 @@ SIGNATURES = {
     "vecchia_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "vecchia_fp64_peak": (ctypes.c_int, [_dp, _vp]),
     "vecchia_loglik_noalloc": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i64, _i32, _dp, _vp, _vp]),
+    "vecchia_batched_prepare": (ctypes.c_int, [_dp, _i32, _vp]),
+    "vecchia_loglik_batched": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i32, _vp, _i32,
+                                              ctypes.c_int, _vp, _vp]),
 }
 
 
@@ -212,6 +217,39 @@ def vecchia_loglik_noalloc(xy: torch.Tensor, y: torch.Tensor, nbr: torch.Tensor,
                                       _vp(_stream(stream)))
     _check(rc, "vecchia_loglik_noalloc")
     return out
+
+
+def vecchia_batched_prepare(nus, stream=None) -> None:
+    """Prepare the covariance tables (one per smoothness value) for the batched call."""
+    arr = (ctypes.c_double * len(nus))(*[float(v) for v in nus])
+    _check(lib().vecchia_batched_prepare(arr, len(nus), _vp(_stream(stream))), "vecchia_batched_prepare")
+
+
+class Batch:
+    """Argument bundle for vecchia_loglik_batched over fixed plans and field arrays."""
+
+    def __init__(self, plans, ys, ntheta: int, want_grad: bool = True):
+        if len(plans) != len(ys):
+            raise ValueError("one field array per plan")
+        self.plans = list(plans)
+        self.ys = [_dev_f64(y, p.n, "y") for p, y in zip(plans, ys)]
+        self.ntheta = int(ntheta)
+        self.want_grad = bool(want_grad)
+        self._ph = (_vp * len(plans))(*[p.handle.value for p in plans])
+        self._yh = (_vp * len(plans))(*[y.data_ptr() for y in self.ys])
+
+    def run(self, thetas: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        nf = len(self.plans)
+        w = 4 if self.want_grad else 1
+        if not (thetas.is_cuda and thetas.dtype == torch.float64 and thetas.is_contiguous()
+                and thetas.numel() == nf * self.ntheta * 4):
+            raise ValueError("thetas must be a contiguous CUDA float64 tensor of shape (nfields, ntheta, 4)")
+        if out is None:
+            out = torch.empty((nf, self.ntheta, w), dtype=torch.float64, device=thetas.device)
+        rc = lib().vecchia_loglik_batched(self._ph, self._yh, nf, _vp(thetas.data_ptr()), self.ntheta,
+                                          1 if self.want_grad else 0, _vp(out.data_ptr()), _vp(_stream(stream)))
+        _check(rc, "vecchia_loglik_batched")
+        return out
 
 
 def vecchia_fp64_peak(stream=None) -> float:

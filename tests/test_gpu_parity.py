@@ -73,12 +73,13 @@ def test_matern_matches_oracle(V, nu):
     # factors (pow, tgamma, K_nu, ...), the table adds its fit (< 1e-16) and Horner rounding.
     err = np.abs(c - want)
     assert np.all(err <= 4e-15 * sigma2), (err.max(), d[np.argmax(err)])
-    # dC/dbeta carries the FP32 tail of the derivative polynomial: below ~1e-9 relative
-    # where the correlation matters (1e-7 would still meet the gradient tolerance), ~1e-7
-    # relative only where the correlation is below 1e-9 (far field).
-    derr = np.abs(dc - wantd)
-    assert np.all(derr <= 2e-9 * np.abs(wantd) + 1e-14 * sigma2 / beta), \
-        (derr.max(), d[np.argmax(derr)], wantd[np.argmax(derr)])
+    # dC/dbeta carries the FP32 tail of the derivative polynomial: ~1e-9 relative where
+    # the correlation exceeds 1e-3, a few 1e-8 relative where it is below 1e-6.  What the
+    # gradient needs is an absolute error small against the largest |dC/dbeta|, so the
+    # bound is 2e-9 relative plus 1e-10 of the largest magnitude.
+    ratio = np.abs(dc - wantd) / (2e-9 * np.abs(wantd) + 1e-10 * np.abs(wantd).max())
+    k = int(np.argmax(ratio))
+    assert ratio[k] <= 1.0, (ratio[k], d[k] / beta, dc[k], wantd[k])
 
 
 # ------------------------------------------------------------------ orderings and kNN
