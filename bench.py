@@ -112,6 +112,67 @@ def make_workload(n, device, rank):
     return xy, y, theta
 
 
+def la_flops_fields(ns, ms, grad: bool) -> float:
+    return sum(la_flops(int(n), int(m), grad) for n, m in zip(ns, ms))
+
+
+def run_batched(V, dev, peak_tflops, nfields=64, ntheta=32, scale=1.0, reps=1):
+    """Many-field workload: nfields uniform fields, n log-uniform in [10k, 500k] (times
+    scale), m uniform on {10, 30, 60}, ntheta candidates per field with nu in
+    {0.5, 1.0, 1.5}; loglik + gradient for every (field, theta) in one persistent launch,
+    captured once in a CUDA graph and replayed."""
+    import torch
+    from paper_2403_07412_gb300 import datagen
+
+    seed = datagen.BASE_SEED + 4
+    ns, ms = datagen.batch_sizes(nfields, seed)
+    ns = np.maximum((ns * scale).astype(np.int64), 100)
+    thetas = datagen.theta_candidates(nfields, ntheta, seed + 1)
+    plans, ys = [], []
+    t0 = time.perf_counter()
+    for f in range(nfields):
+        xy = datagen.uniform_locations(int(ns[f]), seed + 10 + f)
+        y = datagen.field_rff(xy, thetas[f, 0], seed + 1000 + f, device=dev)
+        plans.append(V.Plan(xy, int(ms[f]), order=V.ORDER_RANDOM, seed=seed + 2000 + f))
+        ys.append(torch.as_tensor(y, device=dev))
+    setup_s = time.perf_counter() - t0
+    V.vecchia_batched_prepare([0.5, 1.0, 1.5])
+    b = V.Batch(plans, ys, ntheta, want_grad=True)
+    th = torch.as_tensor(thetas, device=dev).contiguous()
+    out = torch.empty((nfields, ntheta, 4), dtype=torch.float64, device=dev)
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(torch.cuda.current_stream(dev))
+    with torch.cuda.stream(side):
+        b.run(th, out)  # lays out the work (first call), also the warm-up
+    torch.cuda.current_stream(dev).wait_stream(side)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        b.run(th, out)
+    g.replay()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        g.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    ms_rep = e0.elapsed_time(e1) / reps
+    locs = float(ns.sum()) * ntheta
+    flops = la_flops_fields(ns, ms, True) * ntheta
+    achieved = flops / (ms_rep * 1e-3) / 1e12
+    res = out.cpu().numpy()
+    for p in plans:
+        p.close()
+    return {"workload": f"{nfields} fields x {ntheta} thetas, n log-uniform 10k-500k (sum {int(ns.sum())}), "
+                        "m in {10,30,60}, nu in {0.5,1.0,1.5}, uniform locations, random ordering, fwd+grad",
+            "value": locs / (ms_rep * 1e-3), "unit": "locations/s", "ms_per_call": ms_rep,
+            "location_evaluations": int(locs), "graph_replays_timed": reps,
+            "frac_of_fp64_peak": achieved / peak_tflops, "achieved_tflops": achieved,
+            "result_finite": bool(np.all(np.isfinite(res))), "setup_seconds": round(setup_s, 1)}
+
+
 def cpu_baseline(xy, y, theta, m, budget_s):
     """The oracle, as it stands, on a bounded random sample of rows of the same workload
     (its own random ordering and brute-force conditioning sets; neighbour search untimed)."""
@@ -193,6 +254,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle wall time")
     ap.add_argument("--ref-budget", type=float, default=90.0, help="seconds for the whole reference run")
     ap.add_argument("--fwd", action="store_true", help="time the forward-only kernel instead")
+    ap.add_argument("--no-batched", action="store_true", help="skip the many-field batched measurement")
+    ap.add_argument("--batched-scale", type=float, default=1.0, help="scale of the batched fields' sizes")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -292,6 +355,21 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_ms = float(t.item())
 
+    # the plain per-field forward kernel on the same plan
+    fwd_ms = None
+    if not args.fwd:
+        for _ in range(2):
+            V.vecchia_loglik(plan, yd, theta, out=out)
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.steps):
+            V.vecchia_loglik(plan, yd, theta, out=out)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        fwd_ms = f0.elapsed_time(f1) / args.steps
+
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -343,6 +421,13 @@ def main():
         "gpu_launches": 2 * args.steps,
         "clocks": clk.summary(),
     }
+    if fwd_ms is not None:
+        ff = la_flops(n, m, grad=False)
+        line["forward"] = {"kernel": "vecchia_lik_kernel<false> (plain per-field forward)",
+                           "value": n / (fwd_ms * 1e-3), "unit": "locations/s", "ms_per_call": fwd_ms,
+                           "frac_of_fp64_peak": ff / (fwd_ms * 1e-3) / 1e12 / peak}
+    if not args.no_batched:
+        line["batched"] = run_batched(V, dev, peak, scale=args.batched_scale)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(xy, y, theta, m, args.cpu_budget)
     print(json.dumps(line), flush=True)
