@@ -46,6 +46,16 @@ def la_flops(n: int, m: int, grad: bool) -> float:
     return float(f.sum())
 
 
+def kernel_source_hash() -> str:
+    import glob
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2403_07412_gb300", "csrc", "*.cu*"))):
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
 class ClockSampler:
     """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
 
@@ -378,14 +388,16 @@ def main():
     kern_ms = statistics.mean(step_ms)
     achieved = flops / (kern_ms * 1e-3) / 1e12
     peak = peak_gflops / 1e3
-    traffic_path = os.path.join(ROOT, "profiles", "traffic.json")
     traffic = None
+    traffic_path = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(traffic_path):
+        # DRAM bytes per launch from the last ncu capture, valid only for the kernel
+        # sources it was taken on.
         try:
             tj = json.load(open(traffic_path))
             key = "fwd" if args.fwd else "grad"
-            if tj.get("n") == n and tj.get("m") == m and key in tj:
-                traffic = tj[key]
+            if tj.get("n") == n and tj.get("m") == m and tj.get("source_hash") == kernel_source_hash():
+                traffic = tj.get(key)
         except Exception:
             traffic = None
     line = {
