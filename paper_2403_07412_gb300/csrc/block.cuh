@@ -53,27 +53,81 @@ struct SchedSize {
   }
 };
 
-// Per-warp shared-memory area for blocks up to size K.
+// Per-warp shared-memory area for blocks up to size K: the packed triangle A, the
+// block rows' fixed-point coordinates QX, QY and data YV, the pivot column TV and, for
+// the adjoint, the weight vectors WH and GV.
 struct WarpArea {
-  double *A, *X, *Y, *YV, *TV, *H, *WH, *GV;
+  double *A, *YV, *TV, *WH, *GV;
+  long long *QX, *QY;
   __host__ __device__ static int doubles(int K, bool grad) {
     const SchedSize S(K);
     int d = align_up(S.NT, 2) + 4 * align_up(K + 1, 2);
-    if (grad) d += align_up(S.NP, 2) + 2 * align_up(K + 1, 2);
+    if (grad) d += 2 * align_up(K + 1, 2);
     return d;
   }
   __device__ WarpArea(double* base, int K) {
     const SchedSize S(K);
     A = base;
-    X = A + align_up(S.NT, 2);
-    Y = X + align_up(K + 1, 2);
-    YV = Y + align_up(K + 1, 2);
+    QX = reinterpret_cast<long long*>(A + align_up(S.NT, 2));
+    QY = QX + align_up(K + 1, 2);
+    YV = reinterpret_cast<double*>(QY + align_up(K + 1, 2));
     TV = YV + align_up(K + 1, 2);
-    H = TV + align_up(K + 1, 2);
-    WH = H + align_up(S.NP, 2);
+    WH = TV + align_up(K + 1, 2);
     GV = WH + align_up(K + 1, 2);
   }
 };
+
+// Block coordinates as 64-bit fixed point: q = round(v 2^F), with F chosen per block so
+// that every |q| < 2^62.  Differences of fixed-point coordinates are then exact, and the
+// squared distance is formed in 128-bit integer arithmetic and rounded once to FP64:
+// no FP64 instruction per pair (an FP64 path would spend four).
+__device__ __forceinline__ long long to_fixed(double v, int F) {
+  const long long b = __double_as_longlong(v);
+  const int eb = (int)((b >> 52) & 0x7FF);
+  if (eb == 0) return 0;  // zero (or subnormal)
+  const long long mant = (b & 0xFFFFFFFFFFFFFLL) | (1LL << 52);
+  const int sh = eb - 1075 + F;  // v = mant 2^(eb-1075)
+  long long q;
+  if (sh >= 0) q = mant << sh;   // sh <= 9 for the block's largest coordinate
+  else if (sh > -63) q = (mant + (1LL << (-sh - 1))) >> (-sh);
+  else q = 0;
+  return b < 0 ? -q : q;
+}
+
+// (dx^2 + dy^2) 2^(-2F) for fixed-point differences |dx|, |dy| < 2^63, rounded to nearest.
+__device__ __forceinline__ double fixed_sq_dist(long long dx, long long dy, int F) {
+  const unsigned long long ax = (unsigned long long)(dx < 0 ? -dx : dx);
+  const unsigned long long ay = (unsigned long long)(dy < 0 ? -dy : dy);
+  const unsigned long long xl = ax * ax, yl = ay * ay;
+  const unsigned long long lo = xl + yl;
+  const unsigned long long hi = __umul64hi(ax, ax) + __umul64hi(ay, ay) + (lo < xl ? 1ULL : 0ULL);
+  if ((hi | lo) == 0ULL) return 0.0;
+  const int lz = hi ? __clzll((long long)hi) : 64 + __clzll((long long)lo);
+  unsigned long long nh, nl;  // normalised so the leading one is bit 127
+  if (lz >= 64) {
+    nh = lo << (lz - 64);
+    nl = 0ULL;
+  } else if (lz > 0) {
+    nh = (hi << lz) | (lo >> (64 - lz));
+    nl = lo << lz;
+  } else {
+    nh = hi;
+    nl = lo;
+  }
+  unsigned long long mant = nh >> 11;  // 53 bits with the leading one
+  const bool rbit = (nh >> 10) & 1ULL;
+  const bool sticky = (nh & 0x3FFULL) != 0ULL || nl != 0ULL;
+  if (rbit && (sticky || (mant & 1ULL))) mant += 1ULL;
+  int p = 127 - lz;
+  if (mant >> 53) {
+    mant >>= 1;
+    p += 1;
+  }
+  const int eb = 1023 + p - 2 * F;
+  if (eb <= 0) return 0.0;
+  if (eb >= 2047) return __longlong_as_double(0x7FF0000000000000LL);
+  return __longlong_as_double(((long long)eb << 52) | (long long)(mant & 0xFFFFFFFFFFFFFULL));
+}
 
 // Element schedules for block size K: sched[e] = (row, col) of packed slot e;
 // pairs[q] = (row, col, slot) of the q-th strictly-lower pair of the K x K block.
@@ -137,31 +191,47 @@ __device__ __forceinline__ bool process_location(int64_t i, const FieldView& F, 
   const int m = F.m;
   const int K = m + 1;
   double* __restrict__ A = W.A;
-  double* __restrict__ X = W.X;
-  double* __restrict__ Y = W.Y;
+  long long* __restrict__ QX = W.QX;
+  long long* __restrict__ QY = W.QY;
   double* __restrict__ YV = W.YV;
   double* __restrict__ TV = W.TV;
   const int mi = i < m ? (int)i : m;
   const int32_t* __restrict__ row = F.nbr + i * m;
   const int js = F.self[i];
   const double2 ps = F.xy[js];
-  // ---- gather: centred, 1/beta-scaled coordinates and data of the block rows
-  for (int p = lane; p < m; p += 32) {
-    double xv = 0.0, yv = 0.0, fv = 0.0;
-    if (p < mi) {
-      const int j = row[p];
-      const double2 q = F.xy[j];
-      xv = (q.x - ps.x) * tc.inv_beta;
-      yv = (q.y - ps.y) * tc.inv_beta;
-      fv = F.yf[j];
+  // ---- gather: centred, 1/beta-scaled coordinates (then fixed point) and data
+  double xv[2] = {0.0, 0.0}, yv[2] = {0.0, 0.0};
+  int emax = 0;
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    const int p = lane + 32 * s;
+    if (p < m) {
+      double fv = 0.0;
+      if (p < mi) {
+        const int j = row[p];
+        const double2 q = F.xy[j];
+        xv[s] = (q.x - ps.x) * tc.inv_beta;
+        yv[s] = (q.y - ps.y) * tc.inv_beta;
+        fv = F.yf[j];
+      }
+      YV[p] = fv;
+      emax = max(emax, (int)((__double_as_longlong(xv[s]) >> 52) & 0x7FF));
+      emax = max(emax, (int)((__double_as_longlong(yv[s]) >> 52) & 0x7FF));
     }
-    X[p] = xv;
-    Y[p] = yv;
-    YV[p] = fv;
+  }
+  emax = __reduce_max_sync(0xffffffffu, emax);
+  const int FX = emax == 0 ? 0 : 61 - (emax - 1023);  // |coordinate| 2^FX < 2^62
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    const int p = lane + 32 * s;
+    if (p < m) {
+      QX[p] = to_fixed(xv[s], FX);
+      QY[p] = to_fixed(yv[s], FX);
+    }
   }
   if (lane == 0) {
-    X[m] = 0.0;
-    Y[m] = 0.0;
+    QX[m] = 0;
+    QY[m] = 0;
     YV[m] = F.yf[js];
   }
   __syncwarp();
@@ -182,22 +252,15 @@ __device__ __forceinline__ bool process_location(int64_t i, const FieldView& F, 
     const int r1 = w1 & 0xFF, c1 = (w1 >> 8) & 0xFF;
     const bool v0 = c0 < mi && (r0 < mi || r0 == m);
     const bool v1 = has1 && c1 < mi && (r1 < mi || r1 == m);
-    const double dx0 = X[r0] - X[c0], dy0 = Y[r0] - Y[c0];
-    const double dx1 = X[r1] - X[c1], dy1 = Y[r1] - Y[c1];
-    const double u0 = fma(dx0, dx0, dy0 * dy0), u1 = fma(dx1, dx1, dy1 * dy1);
-    double val0, hv0 = 0.0, val1, hv1 = 0.0;
-    rho_poly<GRAD>(u0, tab, val0, hv0);
-    rho_poly<GRAD>(u1, tab, val1, hv1);
+    const double u0 = fixed_sq_dist(QX[r0] - QX[c0], QY[r0] - QY[c0], FX);
+    const double u1 = fixed_sq_dist(QX[r1] - QX[c1], QY[r1] - QY[c1], FX);
+    double val0, hv0, val1, hv1;
+    rho_poly<false>(u0, tab, val0, hv0);
+    rho_poly<false>(u1, tab, val1, hv1);
     rho_fix(u0, mc, val0, hv0);
     rho_fix(u1, mc, val1, hv1);
-    if (!v0) { val0 = 0.0; hv0 = 0.0; }
-    if (!v1) { val1 = 0.0; hv1 = 0.0; }
-    A[w0 >> 16] = val0;
-    if (GRAD) W.H[q0] = hv0;
-    if (has1) {
-      A[w1 >> 16] = val1;
-      if (GRAD) W.H[q1] = hv1;
-    }
+    A[w0 >> 16] = v0 ? val0 : 0.0;
+    if (has1) A[w1 >> 16] = v1 ? val1 : 0.0;
   }
   __syncwarp();
   // ---- L D L^T over the neighbour columns
@@ -319,13 +382,28 @@ __device__ __forceinline__ bool process_location(int64_t i, const FieldView& F, 
   const double sS = 0.5 * (rr * rs - 1.0);
   acc.S += sS;
   __syncwarp();
+  // beta pair sums: h(u_pq) recomputed from the fixed-point coordinates (pads carry
+  // zero weights), two pairs per iteration.
   double pB = 0.0;
-  for (int q = lane; q < S.NP; q += 32) {
-    const uint32_t w = pairs[q];
-    const int r = w & 0xFF, c = (w >> 8) & 0xFF;
-    double t = WH[r] * GV[c];
-    t = fma(WH[c], GV[r], t);
-    pB = fma(W.H[q], t, pB);
+  for (int q0 = lane; q0 < S.NP; q0 += 64) {
+    const int q1 = q0 + 32;
+    const bool has1 = q1 < S.NP;
+    const uint32_t w0 = pairs[q0];
+    const uint32_t w1 = has1 ? pairs[q1] : w0;
+    const int r0 = w0 & 0xFF, c0 = (w0 >> 8) & 0xFF;
+    const int r1 = w1 & 0xFF, c1 = (w1 >> 8) & 0xFF;
+    const double u0 = fixed_sq_dist(QX[r0] - QX[c0], QY[r0] - QY[c0], FX);
+    const double u1 = fixed_sq_dist(QX[r1] - QX[c1], QY[r1] - QY[c1], FX);
+    const double h0 = h_fix(u0, mc, h_poly(u0, tab));
+    const double h1 = h_fix(u1, mc, h_poly(u1, tab));
+    double t0 = WH[r0] * GV[c0];
+    t0 = fma(WH[c0], GV[r0], t0);
+    pB = fma(h0, t0, pB);
+    if (has1) {
+      double t1 = WH[r1] * GV[c1];
+      t1 = fma(WH[c1], GV[r1], t1);
+      pB = fma(h1, t1, pB);
+    }
   }
   if (terms) {
     const double tB = warp_sum(pB), tT = warp_sum(pT);

@@ -136,6 +136,40 @@ __device__ __forceinline__ void rho_poly(double u, const double* __restrict__ ta
   }
 }
 
+// h(u) = u rho'(u) alone (the derivative part of rho_poly<true>), branch-free.
+__device__ __forceinline__ double h_poly(double u, const double* __restrict__ tab) {
+  const long long b = __double_as_longlong(u);
+  const int ex = min(max((int)(b >> 52) - 1023, kELo), kEHi - 1);
+  const int idx = ((ex - kELo) << kSub) | (int)((b >> 49) & 7);
+  const long long fr = b & 0x1FFFFFFFFFFFFLL;
+  const double t = fixed_to_double_2m48(fr - (1LL << 48));
+  const float tf = fmaf(__uint_as_float(0x3F800000u | (unsigned)(fr >> 26)), 2.0f, -3.0f);
+  const double2* __restrict__ cd = reinterpret_cast<const double2*>(table_d(tab) + idx * kNDbl);
+  const float4* __restrict__ cf = reinterpret_cast<const float4*>(table_f(tab) + idx * kNFlt);
+  const double2 c01 = __ldg(cd), c2x = __ldg(cd + 3);
+  const float4 f1 = __ldg(cf + 1), f2 = __ldg(cf + 2);
+  float r = f2.z;
+  r = fmaf(r, tf, f2.y);
+  r = fmaf(r, tf, f2.x);
+  r = fmaf(r, tf, f1.w);
+  r = fmaf(r, tf, f1.z);
+  r = fmaf(r, tf, f1.y);
+  r = fmaf(r, tf, f1.x);
+  const double dq = fma(t, f2d_exact(r), c2x.x);
+  const double dp = fma(t, dq, c01.y);
+  return __longlong_as_double(0x4030000000000000LL | (b & 0xFFFFFFFFFFFFFLL)) * dp;
+}
+
+__device__ __forceinline__ double h_fix(double u, const MaternConst& mc, double h) {
+  const int ex = (int)(__double_as_longlong(u) >> 52) - 1023;
+  if (ex >= kEHi) return 0.0;
+  if (ex < kELo) {
+    double r;
+    rho_small(u, mc, r, h);
+  }
+  return h;
+}
+
 // Replaces rho_poly's value outside the tabulated range (rare): far field -> 0,
 // u < 2^kELo -> expansion at zero.
 __device__ __forceinline__ void rho_fix(double u, const MaternConst& mc, double& rho, double& h) {
