@@ -205,7 +205,7 @@ int batched_config(int fixed_bytes, int per_warp_bytes, int* W, int* blocks, int
   VECCHIA_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   VECCHIA_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   int best = -1;
-  for (int w : {12, 10, 8, 6, 4, 2, 1}) {
+  for (int w : {12, 11, 10, 9, 8, 6, 4, 2, 1}) {
     const int bytes = fixed_bytes + w * per_warp_bytes;
     if (bytes > optin) continue;
     VECCHIA_CUDA_TRY(cudaFuncSetAttribute(vecchia_batched_kernel<GRAD>,

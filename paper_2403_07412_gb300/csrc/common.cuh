@@ -16,12 +16,12 @@ namespace vecchia {
 // local variable t in [-1, 1).  Interval index and t come straight from the bits of u.
 constexpr int kELo = -30;
 constexpr int kEHi = 20;
-constexpr int kSub = 3;
-constexpr int kDeg = 9;
+constexpr int kSub = 4;
+constexpr int kDeg = 8;
 constexpr int kNInt = (kEHi - kELo) << kSub;
-// Per interval: FP64 {c0, c1, c2, c3, c4, c5, 2 c2, 0} and FP32
-// {c6, c7, c8, c9, 3c3, 4c4, 5c5, 6c6, 7c7, 8c8, 9c9, 0} (see matern.cuh).
-constexpr int kNDbl = 8;
+// Per interval: FP64 {c0, c1, c2, c3, c4, 2 c2} and FP32
+// {c5, c6, c7, c8, 3c3, 4c4, 5c5, 6c6, 7c7, 8c8, 0, 0} (see matern.cuh).
+constexpr int kNDbl = 6;
 constexpr int kNFlt = 12;
 // Small-u constants stored after the FP64 coefficients: kind, nu, a1, G, b0, b1, I(0).
 constexpr int kNConst = 8;

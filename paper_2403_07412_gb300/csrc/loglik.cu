@@ -116,7 +116,7 @@ int pick_config(int K, bool grad, LaunchCfg* cfg) {
   // to the larger CTA).  VECCHIA_WARPS_PER_CTA forces one value (tuning experiments).
   const char* fenv = getenv("VECCHIA_WARPS_PER_CTA");
   const int forced = fenv ? atoi(fenv) : 0;
-  const int cand_all[] = {12, 10, 8, 6, 4, 2, 1};
+  const int cand_all[] = {12, 11, 10, 9, 8, 6, 4, 2, 1};
   for (int W : cand_all) {
     if (forced > 0 && W != forced) continue;
     const int bytes = L.bytes(W);

@@ -73,8 +73,8 @@ __global__ void matern_fit_kernel(double nu, double* tab) {
   const int tid = threadIdx.x;
   const double I0 = tab[kNInt * kNDbl + 6];
   const double scale = ldexp(1.0, e);
-  const double mid = scale * (1.0 + (2.0 * j + 1.0) / 16.0);
-  const double hw = scale / 16.0;
+  const double mid = scale * (1.0 + (2.0 * j + 1.0) / (2.0 * (1 << kSub)));
+  const double hw = scale / (2.0 * (1 << kSub));
   if (tid < N) {
     const double tn = cospi((tid + 0.5) / N);
     f[tid] = quad_I(mid + hw * tn, nu) / I0;
@@ -104,12 +104,12 @@ __global__ void matern_fit_kernel(double nu, double* tab) {
   __syncthreads();
   if (tid == 0) {
     double* d = tab + idx * kNDbl;
-    for (int k = 0; k < 6; ++k) d[k] = mono[k];
-    d[6] = 2.0 * mono[2];
-    d[7] = 0.0;
+    for (int k = 0; k <= 4; ++k) d[k] = mono[k];
+    d[5] = 2.0 * mono[2];
     float* fl = reinterpret_cast<float*>(tab + kNInt * kNDbl + kNConst) + idx * kNFlt;
-    for (int k = 6; k <= 9; ++k) fl[k - 6] = (float)mono[k];
-    for (int k = 3; k <= 9; ++k) fl[4 + k - 3] = (float)(k * mono[k]);
+    for (int k = 5; k <= 8; ++k) fl[k - 5] = (float)mono[k];
+    for (int k = 3; k <= 8; ++k) fl[4 + k - 3] = (float)(k * mono[k]);
+    fl[10] = 0.0f;
     fl[11] = 0.0f;
   }
 }

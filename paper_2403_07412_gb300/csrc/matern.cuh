@@ -3,21 +3,20 @@
 // rho(u) = C(d)/sigma2 with u = (d/beta)^2, and h(u) = u * drho/du, so that
 // dC/dbeta = -(2 sigma2 / beta) h(u).  rho is read from a per-nu table of
 // piecewise polynomials (built on the GPU by matern_fit_kernel, see matern.cu):
-//   u in [2^e (1 + j/8), 2^e (1 + (j+1)/8)),  e in [kELo, kEHi),  j in 0..7,
-//   t = 16 u / 2^e - 17 - 2j in [-1, 1),  rho ~ P(t) = sum_{k<=9} c_k t^k.
-// The interval index, t and u dt/du = 16 M (M = mantissa of u) come from the bits of
+//   u in [2^e (1 + j/16), 2^e (1 + (j+1)/16)),  e in [kELo, kEHi),  j in 0..15,
+//   t = 32 u / 2^e - 33 - 2j in [-1, 1),  rho ~ P(t) = sum_{k<=8} c_k t^k.
+// The interval index, t and u dt/du = 32 M (M = mantissa of u) come from the bits of
 // u with integer operations.  On GB300 an FP64 instruction costs as much as ~60 others,
 // so the polynomial is split by magnitude:
-//   P(t) = c0 + t(c1 + t(c2 + t(c3 + t(c4 + t(c5 + t T6(t)))))),
-//   T6(t) = c6 + c7 t + c8 t^2 + c9 t^3 evaluated in FP32;
-//   P'(t) = c1 + t(2 c2 + t R(t)),  R(t) = 3 c3 + 4 c4 t + ... + 9 c9 t^6 in FP32.
-// With |t| <= 1 and coefficients shrinking by ~1/34 per degree near the origin (more
-// slowly in the far field, where rho changes by a large factor across an interval), the
-// FP32 part of rho stays below FP64 rounding (measured: no change to the ~1e-16 absolute
-// error of an all-FP64 Horner), and h keeps ~1e-9 relative accuracy where rho > 1e-3 and
-// a few 1e-8 where rho < 1e-6: absolute errors far below 1e-10 of max |h|, which is what
-// the beta-gradient (a sum of h-weighted pair terms) needs.  FP32 results re-enter FP64
-// by exact bit conversion.  Cost: 6 FP64 FMAs for rho, 3 more FP64 ops for h.
+//   P(t) = c0 + t(c1 + t(c2 + t(c3 + t(c4 + t T5(t))))),
+//   T5(t) = c5 + c6 t + c7 t^2 + c8 t^3 evaluated in FP32;
+//   P'(t) = c1 + t(2 c2 + t R(t)),  R(t) = 3 c3 + 4 c4 t + ... + 8 c8 t^5 in FP32.
+// Near the origin the coefficients shrink by ~1/66 per degree, so the FP32 part of rho
+// stays below FP64 rounding (measured against exact rational evaluation: within
+// 1.7e-16 absolute, as an all-FP64 Horner), and h keeps ~1e-9 relative accuracy where
+// rho > 1e-3 (a few 1e-9 below), far below 1e-10 of max |h| in absolute terms, which
+// is what the beta-gradient (a sum of h-weighted pair terms) needs.  FP32 results
+// re-enter FP64 by exact bit conversion.  Cost: 5 FP64 FMAs for rho, 3 more for h.
 // Below 2^kELo the expansion of rho at u = 0 is used; at and above 2^kEHi, rho = 0.
 #pragma once
 
@@ -61,16 +60,29 @@ __device__ __forceinline__ double f2d_exact(float f) {
   return __longlong_as_double((long long)db);
 }
 
-// t = s 2^-48 for an integer |s| <= 2^48, converted exactly with integer operations
-// (t = 16 u / 2^e - 17 - 2j is this fixed-point value for s = fraction bits - 2^48).
-__device__ __forceinline__ double fixed_to_double_2m48(long long s) {
+// Bits of u below the sub-interval index, and the local variable t = s 2^-kTBits with
+// s = those bits - 2^kTBits (|s| <= 2^kTBits), converted exactly with integer operations.
+constexpr int kFracBits = 52 - kSub;  // bits of u below the sub-interval index
+constexpr int kTBits = kFracBits - 1;
+__device__ __forceinline__ double local_t(long long fr) {
+  const long long s = fr - (1LL << kTBits);
   if (s == 0) return 0.0;
   const unsigned long long sign = s < 0 ? 0x8000000000000000ULL : 0ULL;
   const unsigned long long a = (unsigned long long)(s < 0 ? -s : s);
   const int lz = __clzll((long long)a);             // leading one at bit 63 - lz
-  const unsigned long long e = (unsigned long long)(1023 + (63 - lz) - 48);
+  const unsigned long long e = (unsigned long long)(1023 + (63 - lz) - kTBits);
   const unsigned long long mant = (a << (lz + 1)) >> 12;
   return __longlong_as_double((long long)(sign | (e << 52) | mant));
+}
+
+// The same t in FP32 (23 leading bits), for the FP32 tails.
+__device__ __forceinline__ float local_t_f32(long long fr) {
+  return fmaf(__uint_as_float(0x3F800000u | (unsigned)(fr >> (kFracBits - 23))), 2.0f, -3.0f);
+}
+
+// u dt/du = 2^(kSub+1) M, M = mantissa of u in [1, 2): the exponent field set to 1023+kSub+1.
+__device__ __forceinline__ double u_dtdu(long long b) {
+  return __longlong_as_double(((long long)(1023 + kSub + 1) << 52) | (b & 0xFFFFFFFFFFFFFLL));
 }
 
 // Expansion of rho and h at u -> 0 (u < 2^kELo), from the series of x^nu K_nu(x):
@@ -102,37 +114,33 @@ template <bool DERIV>
 __device__ __forceinline__ void rho_poly(double u, const double* __restrict__ tab, double& rho, double& h) {
   const long long b = __double_as_longlong(u);
   const int ex = min(max((int)(b >> 52) - 1023, kELo), kEHi - 1);
-  const int idx = ((ex - kELo) << kSub) | (int)((b >> 49) & 7);
-  const long long fr = b & 0x1FFFFFFFFFFFFLL;  // bits of u below the sub-interval index
-  const double t = fixed_to_double_2m48(fr - (1LL << 48));
-  const float tf = fmaf(__uint_as_float(0x3F800000u | (unsigned)(fr >> 26)), 2.0f, -3.0f);
+  const int idx = ((ex - kELo) << kSub) | (int)((b >> kFracBits) & ((1 << kSub) - 1));
+  const long long fr = b & ((1LL << kFracBits) - 1);
+  const double t = local_t(fr);
+  const float tf = local_t_f32(fr);
   const double2* __restrict__ cd = reinterpret_cast<const double2*>(table_d(tab) + idx * kNDbl);
   const float4* __restrict__ cf = reinterpret_cast<const float4*>(table_f(tab) + idx * kNFlt);
-  const double2 c01 = __ldg(cd), c23 = __ldg(cd + 1), c45 = __ldg(cd + 2);
+  const double2 c01 = __ldg(cd), c23 = __ldg(cd + 1), c4x = __ldg(cd + 2);
   const float4 f0 = __ldg(cf);
-  const float t6 = fmaf(fmaf(fmaf(f0.w, tf, f0.z), tf, f0.y), tf, f0.x);
-  double p = f2d_exact(t6);
-  p = fma(p, t, c45.y);
-  p = fma(p, t, c45.x);
+  const float t5 = fmaf(fmaf(fmaf(f0.w, tf, f0.z), tf, f0.y), tf, f0.x);
+  double p = f2d_exact(t5);
+  p = fma(p, t, c4x.x);
   p = fma(p, t, c23.y);
   p = fma(p, t, c23.x);
   p = fma(p, t, c01.y);
   rho = fma(p, t, c01.x);
   if (DERIV) {
-    const double2 c2x = __ldg(cd + 3);  // (2 c2, 0)
     const float4 f1 = __ldg(cf + 1), f2 = __ldg(cf + 2);
-    // R(t) = 3c3 + 4c4 t + 5c5 t^2 + 6c6 t^3 + 7c7 t^4 + 8c8 t^5 + 9c9 t^6
-    float r = f2.z;
-    r = fmaf(r, tf, f2.y);
+    // R(t) = 3c3 + 4c4 t + 5c5 t^2 + 6c6 t^3 + 7c7 t^4 + 8c8 t^5
+    float r = f2.y;
     r = fmaf(r, tf, f2.x);
     r = fmaf(r, tf, f1.w);
     r = fmaf(r, tf, f1.z);
     r = fmaf(r, tf, f1.y);
     r = fmaf(r, tf, f1.x);
-    const double dq = fma(t, f2d_exact(r), c2x.x);
+    const double dq = fma(t, f2d_exact(r), c4x.y);
     const double dp = fma(t, dq, c01.y);
-    // u dt/du = 16 M, M = mantissa of u in [1, 2): exponent field set to 1023 + 4.
-    h = __longlong_as_double(0x4030000000000000LL | (b & 0xFFFFFFFFFFFFFLL)) * dp;
+    h = u_dtdu(b) * dp;
   }
 }
 
@@ -140,24 +148,23 @@ __device__ __forceinline__ void rho_poly(double u, const double* __restrict__ ta
 __device__ __forceinline__ double h_poly(double u, const double* __restrict__ tab) {
   const long long b = __double_as_longlong(u);
   const int ex = min(max((int)(b >> 52) - 1023, kELo), kEHi - 1);
-  const int idx = ((ex - kELo) << kSub) | (int)((b >> 49) & 7);
-  const long long fr = b & 0x1FFFFFFFFFFFFLL;
-  const double t = fixed_to_double_2m48(fr - (1LL << 48));
-  const float tf = fmaf(__uint_as_float(0x3F800000u | (unsigned)(fr >> 26)), 2.0f, -3.0f);
+  const int idx = ((ex - kELo) << kSub) | (int)((b >> kFracBits) & ((1 << kSub) - 1));
+  const long long fr = b & ((1LL << kFracBits) - 1);
+  const double t = local_t(fr);
+  const float tf = local_t_f32(fr);
   const double2* __restrict__ cd = reinterpret_cast<const double2*>(table_d(tab) + idx * kNDbl);
   const float4* __restrict__ cf = reinterpret_cast<const float4*>(table_f(tab) + idx * kNFlt);
-  const double2 c01 = __ldg(cd), c2x = __ldg(cd + 3);
+  const double2 c01 = __ldg(cd), c4x = __ldg(cd + 2);
   const float4 f1 = __ldg(cf + 1), f2 = __ldg(cf + 2);
-  float r = f2.z;
-  r = fmaf(r, tf, f2.y);
+  float r = f2.y;
   r = fmaf(r, tf, f2.x);
   r = fmaf(r, tf, f1.w);
   r = fmaf(r, tf, f1.z);
   r = fmaf(r, tf, f1.y);
   r = fmaf(r, tf, f1.x);
-  const double dq = fma(t, f2d_exact(r), c2x.x);
+  const double dq = fma(t, f2d_exact(r), c4x.y);
   const double dp = fma(t, dq, c01.y);
-  return __longlong_as_double(0x4030000000000000LL | (b & 0xFFFFFFFFFFFFFLL)) * dp;
+  return u_dtdu(b) * dp;
 }
 
 __device__ __forceinline__ double h_fix(double u, const MaternConst& mc, double h) {
