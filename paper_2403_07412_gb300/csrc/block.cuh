@@ -155,11 +155,26 @@ struct ThetaConst {
   }
 };
 
-// Running sums of a warp: sum l_i (identical on all lanes), sum 1/2 (r^2/s - 1), and the
-// per-lane partial sums of the beta pair sums and of w^T g.
+// Running sums of a warp.  The log-likelihood is kept as its parts,
+//   sum l_i = -1/2 sum r_i^2/s_i - 1/2 log(prod s_i) - (count) 1/2 log 2 pi,
+// with prod s_i held as a mantissa in [1, 2) and an integer binary exponent, so one
+// log per warp replaces one per location (identical on all lanes).  Also
+// sum 1/2 (r^2/s - 1), and the per-lane partial sums of the beta pair sums and of w^T g.
 struct Accum {
-  Neumaier L;
+  Neumaier Q;
+  double P = 1.0;
+  long long PE = 0;
+  long long count = 0;
   double S = 0.0, B = 0.0, T = 0.0;
+  __device__ __forceinline__ void mul_s(double s) {
+    const long long b = __double_as_longlong(P * s);
+    PE += ((b >> 52) & 0x7FF) - 1023;
+    P = __longlong_as_double((b & 0xFFFFFFFFFFFFFLL) | 0x3FF0000000000000LL);
+  }
+  __device__ __forceinline__ double loglik() const {
+    return -0.5 * Q.value() - 0.5 * (log(P) + 0.69314718055994530942 * (double)PE) -
+           0.91893853320467274178 * (double)count;
+  }
 };
 
 // Field description: device arrays of one field and its plan.
@@ -276,40 +291,45 @@ __device__ __forceinline__ bool process_location(int64_t i, const FieldView& F, 
       A[oj + r - j] = tv * inv;
     }
     __syncwarp();
-    // Trailing update of the prefix [1, oj), four slots per lane per batch: the next
-    // batch's shared-memory loads are issued before this batch's results are stored.
+    // Trailing update of the prefix [1, oj).  Full batches of four slots per lane are
+    // software-pipelined (the next batch's shared-memory loads are issued before this
+    // batch's results are stored); the remainder runs one slot at a time, so no FP64
+    // instruction is issued for a slot that no lane owns.
     const double* Lc = A + oj - j;  // Lc[r] = L[r][j]
     constexpr int U = 4;
-    double lv[U], tv[U], av[U];
-    int ee[U];
-#pragma unroll
-    for (int k = 0; k < U; ++k) {
-      ee[k] = 1 + lane + 32 * k;
-      const int ek = ee[k] < oj ? ee[k] : 0;
-      const uint32_t rc = sched[ek];
-      lv[k] = Lc[rc & 0xFF];
-      tv[k] = TV[rc >> 8];
-      av[k] = A[ek];
-    }
-    for (int base = 1 + lane; base < oj; base += 32 * U) {
-      double res[U];
-#pragma unroll
-      for (int k = 0; k < U; ++k) res[k] = fma(-lv[k], tv[k], av[k]);
-      int ne[U];
+    const int nfull = (oj - 1) / (32 * U);
+    const int tail0 = 1 + 32 * U * nfull;
+    if (nfull > 0) {
+      double lv[U], tv[U], av[U];
 #pragma unroll
       for (int k = 0; k < U; ++k) {
-        ne[k] = base + 32 * (U + k);
-        const int ek = ne[k] < oj ? ne[k] : 0;
-        const uint32_t rc = sched[ek];
+        const uint32_t rc = sched[1 + lane + 32 * k];
         lv[k] = Lc[rc & 0xFF];
         tv[k] = TV[rc >> 8];
-        av[k] = A[ek];
+        av[k] = A[1 + lane + 32 * k];
       }
+      for (int bt = 0; bt < nfull; ++bt) {
+        const int base = 1 + lane + 32 * U * bt;
+        double res[U];
 #pragma unroll
-      for (int k = 0; k < U; ++k) {
-        if (ee[k] < oj) A[ee[k]] = res[k];
-        ee[k] = ne[k];
+        for (int k = 0; k < U; ++k) res[k] = fma(-lv[k], tv[k], av[k]);
+        if (bt + 1 < nfull) {
+#pragma unroll
+          for (int k = 0; k < U; ++k) {
+            const int e = base + 32 * (U + k);
+            const uint32_t rc = sched[e];
+            lv[k] = Lc[rc & 0xFF];
+            tv[k] = TV[rc >> 8];
+            av[k] = A[e];
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < U; ++k) A[base + 32 * k] = res[k];
       }
+    }
+    for (int e = tail0 + lane; e < oj; e += 32) {
+      const uint32_t rc = sched[e];
+      A[e] = fma(-Lc[rc & 0xFF], TV[rc >> 8], A[e]);
     }
     __syncwarp();
   }
@@ -323,14 +343,18 @@ __device__ __forceinline__ bool process_location(int64_t i, const FieldView& F, 
         for (int k = 0; k < tw; ++k) terms[k] = __longlong_as_double(0x7FF8000000000000LL);
       }
     }
-    acc.L.add(__longlong_as_double(0x7FF8000000000000LL));
+    acc.Q.add(__longlong_as_double(0x7FF8000000000000LL));
     __syncwarp();
     return false;
   }
   const double s = tc.sigma2 * st;
   const double inv_s = rcp_newton(s);
-  const double li = -0.5 * rr * rr * inv_s - 0.5 * log(s) - 0.91893853320467274178;
-  acc.L.add(li);
+  const double q = rr * rr * inv_s;
+  acc.Q.add(q);
+  acc.mul_s(s);
+  acc.count += 1;
+  // per-location terms (test and inspection path) pay for their own log
+  const double li = terms ? -0.5 * q - 0.5 * log(s) - 0.91893853320467274178 : 0.0;
   if (!GRAD) {
     if (terms && lane == 0) terms[0] = li;
     __syncwarp();
@@ -425,8 +449,9 @@ __device__ __forceinline__ bool process_location(int64_t i, const FieldView& F, 
 __device__ __forceinline__ void write_partial(Accum& acc, double* out, int lane) {
   const double B = warp_sum(acc.B);
   const double T = warp_sum(acc.T);
+  const double L = acc.loglik();
   if (lane == 0) {
-    out[0] = acc.L.value();
+    out[0] = L;
     out[1] = acc.S;
     out[2] = B;
     out[3] = T;
