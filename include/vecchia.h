@@ -207,6 +207,23 @@ int vecchia_loglik_noalloc(const double* xy_dev, const double* y_dev, const int3
                            double* out_dev, void* stream);
 
 /*
+ * vecchia_autotune — picks the launch shape of the likelihood kernels for this plan's
+ * block size (m + 1) by timing: lanes per location (8, 16 or 32; 32/lanes locations share
+ * a warp) and warps per CTA.  Each candidate is timed on the caller's own problem (two
+ * timed launches after one warm-up; the fastest wins) and recorded, process-wide, for
+ * every later call with the same block size and kind (want_grad) on this device,
+ * including the batched call's layouts created afterwards.  Without tuning, blocks of
+ * up to 16 rows use 8 lanes, up to 32 rows 16 lanes, larger ones a full warp.  Not in
+ * the paper (its batched kernels are library routines).
+ *   y_dev, theta : as for vecchia_loglik (theta on the host).
+ *   lanes_out, warps_out : host int32 (may be NULL): the chosen shape.
+ * Synchronous (waits on `stream`); must not be called during stream capture.
+ * Errors: EINVAL, ENOMEM, ECUDA.
+ */
+int vecchia_autotune(vecchia_plan_t plan, const double* y_dev, const double theta[4], int want_grad,
+                     int32_t* lanes_out, int32_t* warps_out, void* stream);
+
+/*
  * vecchia_last_error_location — synchronises the stream of the plan's last call and
  * reports the first ordered location whose block was not positive definite in that
  * call (*loc = -1 if none).  Returns ENOTPD if there was one, else OK.

@@ -26,6 +26,7 @@ namespace vecchia {
 
 int launch_matern_table(double nu, double* tab, cudaStream_t stream);
 bool theta_ok(const double* th);
+int lanes_for(int K, bool grad);
 
 constexpr int kTile = 256;       // ordered locations per work item
 constexpr int kMaxNu = 8;        // prepared smoothness values
@@ -41,6 +42,7 @@ struct FieldDesc {
   int32_t kidx;       // index of this field's block size in the batch's K list
   int32_t orig;       // position in the caller's field list
   int32_t tiles;      // ceil(n / kTile)
+  int32_t lanes;      // lanes per location (8, 16 or 32)
   int64_t item_base;  // first item of this field
 };
 
@@ -63,6 +65,38 @@ struct BatchArgs {
   int area_off;
   int area_doubles;
 };
+
+// One item with G lanes per location: the 32/G groups of the warp take the tile's
+// locations in turn.
+template <bool GRAD, int G>
+__device__ __forceinline__ void run_item(const FieldDesc& fd, int64_t tile, const unsigned char* smem,
+                                         const BatchArgs& a, double* base, const double* tab,
+                                         const MaternConst& mc, const ThetaConst& tc, double* out, int lane) {
+  constexpr int NL = 32 / G;
+  const int grp = lane / G, sub = lane % G;
+  FieldView F;
+  F.xy = fd.xy;
+  F.yf = fd.yf;
+  F.nbr = fd.nbr;
+  F.self = fd.self;
+  F.n = fd.n;
+  F.m = fd.m;
+  const int K = fd.m + 1;
+  const SchedSize S(K);
+  const uint16_t* sched = reinterpret_cast<const uint16_t*>(smem + a.sched_off[fd.kidx]);
+  const uint32_t* pairs = reinterpret_cast<const uint32_t*>(smem + a.pairs_off[fd.kidx]);
+  const WarpArea area(base + grp * WarpArea::doubles(K, GRAD), K);
+  Accum acc;
+  const int64_t i0 = tile * kTile;
+  const int64_t i1 = min(fd.n, i0 + kTile);
+  for (int64_t b = i0; b < i1; b += NL) {
+    const int64_t i = b + grp;
+    const bool active = i < i1;
+    process_location<GRAD, G>(active ? i : b, active, F, S, sched, pairs, area, tab, mc, tc, acc, false, nullptr,
+                              a.errloc, sub);
+  }
+  write_partial<G>(acc, out, lane);
+}
 
 template <bool GRAD>
 __global__ void __launch_bounds__(384) vecchia_batched_kernel(const BatchArgs a) {
@@ -107,24 +141,9 @@ __global__ void __launch_bounds__(384) vecchia_batched_kernel(const BatchArgs a)
     const MaternConst mc = load_matern_const(tab);
     ThetaConst tc;
     tc.set(s2, beta, t2);
-    FieldView F;
-    F.xy = fd.xy;
-    F.yf = fd.yf;
-    F.nbr = fd.nbr;
-    F.self = fd.self;
-    F.n = fd.n;
-    F.m = fd.m;
-    const int K = fd.m + 1;
-    const SchedSize S(K);
-    const uint16_t* sched = reinterpret_cast<const uint16_t*>(smem + a.sched_off[fd.kidx]);
-    const uint32_t* pairs = reinterpret_cast<const uint32_t*>(smem + a.pairs_off[fd.kidx]);
-    const WarpArea area(base, K);
-    Accum acc;
-    const int64_t i0 = tile * kTile;
-    const int64_t i1 = min(fd.n, i0 + kTile);
-    for (int64_t i = i0; i < i1; ++i)
-      process_location<GRAD>(i, F, S, sched, pairs, area, tab, mc, tc, acc, nullptr, a.errloc, lane);
-    write_partial(acc, out, lane);
+    if (fd.lanes == 8) run_item<GRAD, 8>(fd, tile, smem, a, base, tab, mc, tc, out, lane);
+    else if (fd.lanes == 16) run_item<GRAD, 16>(fd, tile, smem, a, base, tab, mc, tc, out, lane);
+    else run_item<GRAD, 32>(fd, tile, smem, a, base, tab, mc, tc, out, lane);
     __syncwarp();
   }
 }
@@ -256,6 +275,7 @@ int build_batch(const Plan* const* plans, const double* const* ys, int nfields, 
       it = kvals.end() - 1;
     }
     d.kidx = (int)(it - kvals.begin());
+    d.lanes = lanes_for(K, want_grad != 0);
     d.orig = order[s];
     d.tiles = (int)((p->n + kTile - 1) / kTile);
     d.item_base = items;
@@ -271,7 +291,7 @@ int build_batch(const Plan* const* plans, const double* const* ys, int nfields, 
   a.ntheta = ntheta;
   a.total_items = items;
   a.nk = (int)kvals.size();
-  int off = 0, kmax = 0;
+  int off = 0, area = 0;
   for (int k = 0; k < a.nk; ++k) {
     const SchedSize S(kvals[k]);
     a.kval[k] = kvals[k];
@@ -279,10 +299,11 @@ int build_batch(const Plan* const* plans, const double* const* ys, int nfields, 
     off += S.sched_bytes;
     a.pairs_off[k] = off;
     off += S.pairs_bytes;
-    kmax = std::max(kmax, kvals[k]);
   }
+  for (int f = 0; f < nfields; ++f)  // a warp holds 32/lanes blocks of its field's size
+    area = std::max(area, (32 / fd[f].lanes) * WarpArea::doubles(fd[f].m + 1, want_grad != 0));
   a.area_off = off;
-  a.area_doubles = WarpArea::doubles(kmax, want_grad != 0);
+  a.area_doubles = area;
   int rc = want_grad ? batched_config<true>(off, a.area_doubles * 8, &b->W, &b->blocks, &b->smem)
                      : batched_config<false>(off, a.area_doubles * 8, &b->W, &b->blocks, &b->smem);
   if (rc) { delete b; return rc; }

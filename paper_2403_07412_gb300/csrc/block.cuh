@@ -193,16 +193,28 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Processes ordered location i of field F.  terms (optional) receives l_i, or
-// {l_i, dl_i/dsigma2, dl_i/dbeta, dl_i/dtau2} when GRAD.  Returns false when the block
-// was not positive definite (the term is then NaN and i is recorded in errloc).
-template <bool GRAD>
-__device__ __forceinline__ bool process_location(int64_t i, const FieldView& F, const SchedSize& S,
+// Lanes of a group of G lanes (G divides 32): shuffles and reductions stay in the group.
+template <int G>
+__device__ __forceinline__ double group_sum(double v) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, G);
+  return v;
+}
+
+// Processes ordered location i of field F with a group of G lanes (sub = lane within
+// the group); the 32/G groups of a warp run the same instruction stream on different
+// locations, so every loop below has a trip count that depends on K only and no group
+// leaves early; inactive groups (active = false) compute a valid location and discard
+// it.  When terms_mode (the same for the whole warp), terms (if not null) receives l_i,
+// or {l_i, dl_i/dsigma2, dl_i/dbeta, dl_i/dtau2} when GRAD.  A block that is not positive definite gives a NaN term and records i in errloc.
+template <bool GRAD, int G>
+__device__ __forceinline__ void process_location(int64_t i, bool active, const FieldView& F, const SchedSize& S,
                                                  const uint16_t* __restrict__ sched,
                                                  const uint32_t* __restrict__ pairs, const WarpArea& W,
                                                  const double* __restrict__ tab, const MaternConst& mc,
-                                                 const ThetaConst& tc, Accum& acc, double* terms,
-                                                 unsigned long long* errloc, int lane) {
+                                                 const ThetaConst& tc, Accum& acc, bool terms_mode,
+                                                 double* terms, unsigned long long* errloc, int sub) {
+  constexpr int NSG = (kMaxM + G) / G;  // neighbour slots per lane (m <= kMaxM)
   const int m = F.m;
   const int K = m + 1;
   double* __restrict__ A = W.A;
@@ -215,11 +227,13 @@ __device__ __forceinline__ bool process_location(int64_t i, const FieldView& F, 
   const int js = F.self[i];
   const double2 ps = F.xy[js];
   // ---- gather: centred, 1/beta-scaled coordinates (then fixed point) and data
-  double xv[2] = {0.0, 0.0}, yv[2] = {0.0, 0.0};
+  double xv[NSG], yv[NSG];
   int emax = 0;
 #pragma unroll
-  for (int s = 0; s < 2; ++s) {
-    const int p = lane + 32 * s;
+  for (int s = 0; s < NSG; ++s) {
+    const int p = sub + G * s;
+    xv[s] = 0.0;
+    yv[s] = 0.0;
     if (p < m) {
       double fv = 0.0;
       if (p < mi) {
@@ -234,32 +248,33 @@ __device__ __forceinline__ bool process_location(int64_t i, const FieldView& F, 
       emax = max(emax, (int)((__double_as_longlong(yv[s]) >> 52) & 0x7FF));
     }
   }
-  emax = __reduce_max_sync(0xffffffffu, emax);
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o, G));
   const int FX = emax == 0 ? 0 : 61 - (emax - 1023);  // |coordinate| 2^FX < 2^62
 #pragma unroll
-  for (int s = 0; s < 2; ++s) {
-    const int p = lane + 32 * s;
+  for (int s = 0; s < NSG; ++s) {
+    const int p = sub + G * s;
     if (p < m) {
       QX[p] = to_fixed(xv[s], FX);
       QY[p] = to_fixed(yv[s], FX);
     }
   }
-  if (lane == 0) {
+  if (sub == 0) {
     QX[m] = 0;
     QY[m] = 0;
     YV[m] = F.yf[js];
   }
   __syncwarp();
   // ---- assemble: diagonal, data border, then the correlation pairs
-  for (int c = lane; c < K; c += 32) {
+  for (int c = sub; c < K; c += G) {
     const int o = tri_off(K, c);
     A[o] = (c >= mi && c < m) ? 1.0 : tc.gamma1;
     A[o + K - c] = YV[c];
   }
-  if (lane == 0) A[0] = 0.0;
+  if (sub == 0) A[0] = 0.0;
   // Two pairs per lane per iteration so one pair's loads overlap the other's FMAs.
-  for (int q0 = lane; q0 < S.NP; q0 += 64) {
-    const int q1 = q0 + 32;
+  for (int q0 = sub; q0 < S.NP; q0 += 2 * G) {
+    const int q1 = q0 + G;
     const bool has1 = q1 < S.NP;
     const uint32_t w0 = pairs[q0];
     const uint32_t w1 = has1 ? pairs[q1] : w0;
@@ -283,9 +298,9 @@ __device__ __forceinline__ bool process_location(int64_t i, const FieldView& F, 
   for (int j = 0; j < K - 1; ++j) {
     const int oj = tri_off(K, j);
     const double d = A[oj];
-    if (!positive_finite(d)) { ok = false; break; }
+    ok = ok && positive_finite(d);  // a failed block runs on (values unused) to stay in step
     const double inv = rcp_newton(d);
-    for (int r = j + 1 + lane; r <= K; r += 32) {
+    for (int r = j + 1 + sub; r <= K; r += G) {
       const double tv = A[oj + r - j];
       TV[r] = tv;
       A[oj + r - j] = tv * inv;
@@ -297,26 +312,26 @@ __device__ __forceinline__ bool process_location(int64_t i, const FieldView& F, 
     // instruction is issued for a slot that no lane owns.
     const double* Lc = A + oj - j;  // Lc[r] = L[r][j]
     constexpr int U = 4;
-    const int nfull = (oj - 1) / (32 * U);
-    const int tail0 = 1 + 32 * U * nfull;
+    const int nfull = (oj - 1) / (G * U);
+    const int tail0 = 1 + G * U * nfull;
     if (nfull > 0) {
       double lv[U], tv[U], av[U];
 #pragma unroll
       for (int k = 0; k < U; ++k) {
-        const uint32_t rc = sched[1 + lane + 32 * k];
+        const uint32_t rc = sched[1 + sub + G * k];
         lv[k] = Lc[rc & 0xFF];
         tv[k] = TV[rc >> 8];
-        av[k] = A[1 + lane + 32 * k];
+        av[k] = A[1 + sub + G * k];
       }
       for (int bt = 0; bt < nfull; ++bt) {
-        const int base = 1 + lane + 32 * U * bt;
+        const int base = 1 + sub + G * U * bt;
         double res[U];
 #pragma unroll
         for (int k = 0; k < U; ++k) res[k] = fma(-lv[k], tv[k], av[k]);
         if (bt + 1 < nfull) {
 #pragma unroll
           for (int k = 0; k < U; ++k) {
-            const int e = base + 32 * (U + k);
+            const int e = base + G * (U + k);
             const uint32_t rc = sched[e];
             lv[k] = Lc[rc & 0xFF];
             tv[k] = TV[rc >> 8];
@@ -324,10 +339,10 @@ __device__ __forceinline__ bool process_location(int64_t i, const FieldView& F, 
           }
         }
 #pragma unroll
-        for (int k = 0; k < U; ++k) A[base + 32 * k] = res[k];
+        for (int k = 0; k < U; ++k) A[base + G * k] = res[k];
       }
     }
-    for (int e = tail0 + lane; e < oj; e += 32) {
+    for (int e = tail0 + sub; e < oj; e += G) {
       const uint32_t rc = sched[e];
       A[e] = fma(-Lc[rc & 0xFF], TV[rc >> 8], A[e]);
     }
@@ -335,82 +350,91 @@ __device__ __forceinline__ bool process_location(int64_t i, const FieldView& F, 
   }
   const double st = A[1];  // s_i / sigma2
   const double rr = A[2];  // y_i - mu_i
-  if (!ok || !positive_finite(st)) {
-    if (lane == 0) {
-      atomicMin(errloc, (unsigned long long)i);
-      if (terms) {
-        const int tw = GRAD ? 4 : 1;
-        for (int k = 0; k < tw; ++k) terms[k] = __longlong_as_double(0x7FF8000000000000LL);
-      }
-    }
-    acc.Q.add(__longlong_as_double(0x7FF8000000000000LL));
-    __syncwarp();
-    return false;
-  }
+  const bool good = ok && positive_finite(st);
+  const double nan = __longlong_as_double(0x7FF8000000000000LL);
   const double s = tc.sigma2 * st;
   const double inv_s = rcp_newton(s);
   const double q = rr * rr * inv_s;
-  acc.Q.add(q);
-  acc.mul_s(s);
-  acc.count += 1;
+  if (active) {
+    if (good) {
+      acc.Q.add(q);
+      acc.mul_s(s);
+      acc.count += 1;
+    } else {
+      acc.Q.add(nan);
+      if (sub == 0) atomicMin(errloc, (unsigned long long)i);
+    }
+  }
   // per-location terms (test and inspection path) pay for their own log
-  const double li = terms ? -0.5 * q - 0.5 * log(s) - 0.91893853320467274178 : 0.0;
+  const double li = terms_mode ? (good ? -0.5 * q - 0.5 * log(s) - 0.91893853320467274178 : nan) : 0.0;
   if (!GRAD) {
-    if (terms && lane == 0) terms[0] = li;
+    if (terms && active && sub == 0) terms[0] = li;
     __syncwarp();
-    return true;
+    return;
   }
   // ---- adjoint: w = L_J^{-T} (row m of L), alpha~ = L_J^{-T} (row K of L)
   double* __restrict__ WH = W.WH;
   double* __restrict__ GV = W.GV;
-  double w0 = 0.0, w1 = 0.0, b0 = 0.0, b1 = 0.0;
-  const int c0 = lane, c1 = lane + 32;
-  if (c0 < K - 1) { const int o = tri_off(K, c0); w0 = A[o + m - c0]; b0 = A[o + K - c0]; }
-  if (c1 < K - 1) { const int o = tri_off(K, c1); w1 = A[o + m - c1]; b1 = A[o + K - c1]; }
-  for (int c = K - 2; c >= 1; --c) {
-    const int src = c & 31;
-    const double wc = __shfl_sync(0xffffffffu, c >= 32 ? w1 : w0, src);
-    const double bc = __shfl_sync(0xffffffffu, c >= 32 ? b1 : b0, src);
-    if (c0 < c) {
-      const double l = A[tri_off(K, c0) + c - c0];
-      w0 = fma(-l, wc, w0);
-      b0 = fma(-l, bc, b0);
+  constexpr int NS = (kMaxM + G - 1) / G;  // slots of the K-1 <= kMaxM neighbour entries
+  double w[NS], bv[NS];
+#pragma unroll
+  for (int t = 0; t < NS; ++t) {
+    const int c = sub + G * t;
+    w[t] = 0.0;
+    bv[t] = 0.0;
+    if (c < K - 1) {
+      const int o = tri_off(K, c);
+      w[t] = A[o + m - c];
+      bv[t] = A[o + K - c];
     }
-    if (c1 < c) {
-      const double l = A[tri_off(K, c1) + c - c1];
-      w1 = fma(-l, wc, w1);
-      b1 = fma(-l, bc, b1);
+  }
+  for (int c = K - 2; c >= 1; --c) {
+    const int src = c % G, sl = c / G;
+    double wsel = w[0], bsel = bv[0];
+#pragma unroll
+    for (int t = 1; t < NS; ++t)
+      if (sl == t) {
+        wsel = w[t];
+        bsel = bv[t];
+      }
+    const double wc = __shfl_sync(0xffffffffu, wsel, src, G);
+    const double bc = __shfl_sync(0xffffffffu, bsel, src, G);
+#pragma unroll
+    for (int t = 0; t < NS; ++t) {
+      const int cc = sub + G * t;
+      if (cc < c) {
+        const double l = A[tri_off(K, cc) + c - cc];
+        w[t] = fma(-l, wc, w[t]);
+        bv[t] = fma(-l, bc, bv[t]);
+      }
     }
   }
   const double rs = rr * inv_s;
   const double cb = 0.5 * (rs * rs - inv_s);
   const double rsa = rs * tc.inv_sigma2;  // alpha = alpha~ / sigma2
   double pT = 0.0;
-  if (c0 < K - 1) {
-    const double wh = -w0, gv = fma(rsa, b0, cb * wh);
-    WH[c0] = wh;
-    GV[c0] = gv;
-    pT = fma(wh, gv, pT);
+#pragma unroll
+  for (int t = 0; t < NS; ++t) {
+    const int c = sub + G * t;
+    if (c < K - 1) {
+      const double wh = -w[t], gv = fma(rsa, bv[t], cb * wh);
+      WH[c] = wh;
+      GV[c] = gv;
+      pT = fma(wh, gv, pT);
+    }
   }
-  if (c1 < K - 1) {
-    const double wh = -w1, gv = fma(rsa, b1, cb * wh);
-    WH[c1] = wh;
-    GV[c1] = gv;
-    pT = fma(wh, gv, pT);
-  }
-  if (lane == 0) {
+  if (sub == 0) {
     WH[m] = 1.0;
     GV[m] = cb;
     pT += cb;
   }
   const double sS = 0.5 * (rr * rs - 1.0);
-  acc.S += sS;
   __syncwarp();
   // beta pair sums: h(u_pq) recomputed from the fixed-point coordinates (pads carry
   // zero weights), two pairs per iteration.
   double pB = 0.0;
-  for (int q0 = lane; q0 < S.NP; q0 += 64) {
-    const int q1 = q0 + 32;
+  for (int q0 = sub; q0 < S.NP; q0 += 2 * G) {
+    const int q1 = q0 + G;
     const bool has1 = q1 < S.NP;
     const uint32_t w0 = pairs[q0];
     const uint32_t w1 = has1 ? pairs[q1] : w0;
@@ -429,30 +453,44 @@ __device__ __forceinline__ bool process_location(int64_t i, const FieldView& F, 
       pB = fma(h1, t1, pB);
     }
   }
-  if (terms) {
-    const double tB = warp_sum(pB), tT = warp_sum(pT);
-    if (lane == 0) {
+  if (terms_mode) {
+    const double tB = group_sum<G>(pB), tT = group_sum<G>(pT);
+    if (terms && active && sub == 0) {
       terms[0] = li;
-      terms[1] = (sS - tc.tau2 * tT) * tc.inv_sigma2;
-      terms[2] = -2.0 * tc.sigma2 * tc.inv_beta * tB;
-      terms[3] = tT;
+      terms[1] = good ? (sS - tc.tau2 * tT) * tc.inv_sigma2 : nan;
+      terms[2] = good ? -2.0 * tc.sigma2 * tc.inv_beta * tB : nan;
+      terms[3] = good ? tT : nan;
     }
   }
-  acc.B += pB;
-  acc.T += pT;
+  if (active) {
+    if (good) {
+      acc.S += sS;
+      acc.B += pB;
+      acc.T += pT;
+    } else {
+      acc.S += nan;
+    }
+  }
   __syncwarp();
-  return true;
 }
 
-// Converts a warp's (reduced) sums into the four output slots
-// {l, sum 1/2(r^2/s - 1), sum of beta pair sums, sum w^T g}.
+// Combines the warp's sums into the four output slots
+// {l, sum 1/2(r^2/s - 1), sum of beta pair sums, sum w^T g}: per-group values are
+// added over the 32/G groups in group order, per-lane partials over all lanes.
+template <int G>
 __device__ __forceinline__ void write_partial(Accum& acc, double* out, int lane) {
   const double B = warp_sum(acc.B);
   const double T = warp_sum(acc.T);
-  const double L = acc.loglik();
+  const double Lg = acc.loglik();
+  double L = Lg, Ssum = acc.S;
+#pragma unroll
+  for (int g = 1; g < 32 / G; ++g) {
+    L += __shfl_sync(0xffffffffu, Lg, g * G);
+    Ssum += __shfl_sync(0xffffffffu, acc.S, g * G);
+  }
   if (lane == 0) {
     out[0] = L;
-    out[1] = acc.S;
+    out[1] = Ssum;
     out[2] = B;
     out[3] = T;
   }

@@ -9,6 +9,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <mutex>
+#include <vector>
 
 #include "block.cuh"
 #include "common.cuh"
@@ -34,26 +35,30 @@ struct LikArgs {
   unsigned long long* errloc;
 };
 
-// Shared-memory layout for block size K (= m + 1) and W warps per CTA.
+// Shared-memory layout for block size K (= m + 1), G lanes per location (32/G locations
+// per warp) and W warps per CTA.
 struct SmemLayout {
   SchedSize S;
-  int per_warp_doubles;
-  __host__ __device__ SmemLayout(int K, bool grad) : S(K), per_warp_doubles(WarpArea::doubles(K, grad)) {}
+  int group_doubles, per_warp_doubles;
+  __host__ __device__ SmemLayout(int K, bool grad, int G)
+      : S(K), group_doubles(WarpArea::doubles(K, grad)), per_warp_doubles((32 / G) * WarpArea::doubles(K, grad)) {}
   __host__ __device__ int bytes(int W) const { return S.sched_bytes + S.pairs_bytes + W * per_warp_doubles * 8; }
 };
 
-template <bool GRAD>
+template <bool GRAD, int G>
 __global__ void __launch_bounds__(384) vecchia_lik_kernel(const LikArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int NL = 32 / G;
   const int K = a.m + 1;
-  const SmemLayout L(K, GRAD);
+  const SmemLayout L(K, GRAD, G);
   uint16_t* sched = reinterpret_cast<uint16_t*>(smem);
   uint32_t* pairs = reinterpret_cast<uint32_t*>(smem + L.S.sched_bytes);
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   const int W = blockDim.x >> 5;
+  const int grp = lane / G, sub = lane % G;
   const WarpArea area(reinterpret_cast<double*>(smem + L.S.sched_bytes + L.S.pairs_bytes) +
-                          wib * L.per_warp_doubles, K);
+                          wib * L.per_warp_doubles + grp * L.group_doubles, K);
   build_schedules(K, sched, pairs);
   __syncthreads();
 
@@ -69,12 +74,17 @@ __global__ void __launch_bounds__(384) vecchia_lik_kernel(const LikArgs a) {
   F.m = a.m;
   const int64_t gw = (int64_t)blockIdx.x * W + wib;
   const int64_t nw = (int64_t)gridDim.x * W;
+  const bool terms_mode = a.terms != nullptr;
   Accum acc;
-  for (int64_t i = gw; i < a.n; i += nw) {
-    double* trow = a.terms ? a.terms + i * (GRAD ? 4 : 1) : nullptr;
-    process_location<GRAD>(i, F, L.S, sched, pairs, area, a.tab, mc, tc, acc, trow, a.errloc, lane);
+  for (int64_t base = gw * NL; base < a.n; base += nw * NL) {
+    const int64_t i = base + grp;
+    const bool active = i < a.n;
+    const int64_t ii = active ? i : base;
+    double* trow = terms_mode ? a.terms + ii * (GRAD ? 4 : 1) : nullptr;
+    process_location<GRAD, G>(ii, active, F, L.S, sched, pairs, area, a.tab, mc, tc, acc, terms_mode, trow,
+                              a.errloc, sub);
   }
-  write_partial(acc, a.partial + gw * 4, lane);
+  write_partial<G>(acc, a.partial + gw * 4, lane);
 }
 
 // Deterministic reduction of the per-warp partials (fixed order, Neumaier).
@@ -102,51 +112,123 @@ __global__ void vecchia_finalize_kernel(const double* __restrict__ partial, int6
 // ------------------------------------------------------------------ launch
 namespace {
 struct LaunchCfg {
-  int W = 4, blocks = 0, smem = 0;
+  int G = 32, W = 4, blocks = 0, smem = 0;
 };
 
-int pick_config(int K, bool grad, LaunchCfg* cfg) {
+template <bool GRAD, int G>
+void* kernel_ptr() {
+  return reinterpret_cast<void*>(vecchia_lik_kernel<GRAD, G>);
+}
+
+void* lik_kernel(bool grad, int G) {
+  if (grad) return G == 8 ? kernel_ptr<true, 8>() : G == 16 ? kernel_ptr<true, 16>() : kernel_ptr<true, 32>();
+  return G == 8 ? kernel_ptr<false, 8>() : G == 16 ? kernel_ptr<false, 16>() : kernel_ptr<false, 32>();
+}
+
+// Lanes per location chosen when no tuning result exists: small blocks share a warp.
+int default_lanes(int K) { return K <= 16 ? 8 : (K <= 32 ? 16 : 32); }
+
+// Tuning results, per (device, K, grad): lanes per location and warps per CTA.
+struct Tuned {
+  int dev, K, grad, G, W;
+};
+std::mutex g_tune_mu;
+std::vector<Tuned> g_tuned;
+
+bool tuned_for(int dev, int K, bool grad, int* G, int* W) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  for (const Tuned& t : g_tuned)
+    if (t.dev == dev && t.K == K && t.grad == (int)grad) {
+      *G = t.G;
+      *W = t.W;
+      return true;
+    }
+  return false;
+}
+
+void set_tuned(int dev, int K, bool grad, int G, int W) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  for (Tuned& t : g_tuned)
+    if (t.dev == dev && t.K == K && t.grad == (int)grad) {
+      t.G = G;
+      t.W = W;
+      return;
+    }
+  g_tuned.push_back({dev, K, (int)grad, G, W});
+}
+
+// Launch shape for lanes-per-location G: W (forced_W > 0, else the value giving the most
+// resident warps per SM, ties to the larger CTA) and a persistent grid of one wave.
+int shape_for(int K, bool grad, int G, int forced_W, LaunchCfg* cfg) {
   int dev = 0, sms = 0, smem_optin = 0;
   VECCHIA_CUDA_TRY(cudaGetDevice(&dev));
   VECCHIA_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   VECCHIA_CUDA_TRY(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  const SmemLayout L(K, grad);
+  const SmemLayout L(K, grad, G);
+  void* kern = lik_kernel(grad, G);
   int best_warps = -1;
-  // Warps per CTA: the candidate giving the most resident warps per SM wins (ties go
-  // to the larger CTA).  VECCHIA_WARPS_PER_CTA forces one value (tuning experiments).
-  const char* fenv = getenv("VECCHIA_WARPS_PER_CTA");
-  const int forced = fenv ? atoi(fenv) : 0;
-  const int cand_all[] = {12, 11, 10, 9, 8, 6, 4, 2, 1};
-  for (int W : cand_all) {
-    if (forced > 0 && W != forced) continue;
+  for (int W : {12, 11, 10, 9, 8, 6, 4, 2, 1}) {
+    if (forced_W > 0 && W != forced_W) continue;
     const int bytes = L.bytes(W);
     if (bytes > smem_optin) continue;
-    auto kern = grad ? vecchia_lik_kernel<true> : vecchia_lik_kernel<false>;
     VECCHIA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
     int per_sm = 0;
     VECCHIA_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, W * 32, bytes));
     const int warps = std::min(per_sm * W, 16);
     if (per_sm > 0 && warps > best_warps) {
       best_warps = warps;
+      cfg->G = G;
       cfg->W = W;
       cfg->blocks = per_sm * sms;
       cfg->smem = bytes;
     }
   }
   if (best_warps <= 0) return VECCHIA_EINVAL;
-  auto kern = grad ? vecchia_lik_kernel<true> : vecchia_lik_kernel<false>;
   VECCHIA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, cfg->smem));
   return VECCHIA_OK;
 }
+
+// Configuration for block size K: the tuned shape if vecchia_autotune recorded one, else
+// the default lanes per location.  VECCHIA_LANES_PER_LOCATION / VECCHIA_WARPS_PER_CTA
+// force either value (tuning experiments).
+int pick_config(int K, bool grad, LaunchCfg* cfg) {
+  int dev = 0;
+  VECCHIA_CUDA_TRY(cudaGetDevice(&dev));
+  int G = default_lanes(K), W = 0;
+  tuned_for(dev, K, grad, &G, &W);
+  if (const char* e = getenv("VECCHIA_LANES_PER_LOCATION")) {
+    const int v = atoi(e);
+    if (v == 8 || v == 16 || v == 32) G = v;
+  }
+  if (const char* e = getenv("VECCHIA_WARPS_PER_CTA")) W = atoi(e);
+  return shape_for(K, grad, G, W, cfg);
+}
+
+void launch_lik(const LaunchCfg& cfg, bool grad, const LikArgs& a, cudaStream_t stream) {
+  if (grad) {
+    if (cfg.G == 8) vecchia_lik_kernel<true, 8><<<cfg.blocks, cfg.W * 32, cfg.smem, stream>>>(a);
+    else if (cfg.G == 16) vecchia_lik_kernel<true, 16><<<cfg.blocks, cfg.W * 32, cfg.smem, stream>>>(a);
+    else vecchia_lik_kernel<true, 32><<<cfg.blocks, cfg.W * 32, cfg.smem, stream>>>(a);
+  } else {
+    if (cfg.G == 8) vecchia_lik_kernel<false, 8><<<cfg.blocks, cfg.W * 32, cfg.smem, stream>>>(a);
+    else if (cfg.G == 16) vecchia_lik_kernel<false, 16><<<cfg.blocks, cfg.W * 32, cfg.smem, stream>>>(a);
+    else vecchia_lik_kernel<false, 32><<<cfg.blocks, cfg.W * 32, cfg.smem, stream>>>(a);
+  }
+}
 }  // namespace
 
-int launch_loglik(Plan* p, const double* y_dev, const double* theta, bool grad, double* out_dev,
-                  double* terms_dev, cudaStream_t stream) {
-  if (!p || !y_dev || !theta_ok(theta) || (!out_dev && !terms_dev)) return VECCHIA_EINVAL;
-  const int K = p->m + 1;
-  LaunchCfg cfg;
-  int rc = pick_config(K, grad, &cfg);
-  if (rc) return rc;
+// Lanes per location for block size K: the tuned value if any, else the default.
+int lanes_for(int K, bool grad) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return default_lanes(K);
+  int G = default_lanes(K), W = 0;
+  tuned_for(dev, K, grad, &G, &W);
+  return G;
+}
+
+namespace {
+int launch_with(Plan* p, const double* y_dev, const double* theta, bool grad, const LaunchCfg& cfg,
+                double* out_dev, double* terms_dev, cudaStream_t stream) {
   const int64_t nw = (int64_t)cfg.blocks * cfg.W;
   if (p->partial_cap < nw * 4) {
     if (p->d_partial) cudaFree(p->d_partial);
@@ -156,7 +238,7 @@ int launch_loglik(Plan* p, const double* y_dev, const double* theta, bool grad, 
     p->partial_cap = nw * 4;
   }
   const double* tab = nullptr;
-  rc = get_matern_table(theta[2], stream, &tab);
+  int rc = get_matern_table(theta[2], stream, &tab);
   if (rc) return rc;
   VECCHIA_CUDA_TRY(cudaMemsetAsync(p->d_errloc, 0xFF, sizeof(unsigned long long), stream));
   LikArgs a;
@@ -173,8 +255,7 @@ int launch_loglik(Plan* p, const double* y_dev, const double* theta, bool grad, 
   a.partial = p->d_partial;
   a.terms = terms_dev;
   a.errloc = p->d_errloc;
-  if (grad) vecchia_lik_kernel<true><<<cfg.blocks, cfg.W * 32, cfg.smem, stream>>>(a);
-  else vecchia_lik_kernel<false><<<cfg.blocks, cfg.W * 32, cfg.smem, stream>>>(a);
+  launch_lik(cfg, grad, a, stream);
   VECCHIA_CUDA_TRY(cudaGetLastError());
   if (out_dev) {
     vecchia_finalize_kernel<<<1, 32, 0, stream>>>(p->d_partial, nw, theta[0], theta[1], theta[3], grad ? 1 : 0,
@@ -182,6 +263,64 @@ int launch_loglik(Plan* p, const double* y_dev, const double* theta, bool grad, 
     VECCHIA_CUDA_TRY(cudaGetLastError());
   }
   p->last_stream = stream;
+  return VECCHIA_OK;
+}
+}  // namespace
+
+int launch_loglik(Plan* p, const double* y_dev, const double* theta, bool grad, double* out_dev,
+                  double* terms_dev, cudaStream_t stream) {
+  if (!p || !y_dev || !theta_ok(theta) || (!out_dev && !terms_dev)) return VECCHIA_EINVAL;
+  LaunchCfg cfg;
+  int rc = pick_config(p->m + 1, grad, &cfg);
+  if (rc) return rc;
+  return launch_with(p, y_dev, theta, grad, cfg, out_dev, terms_dev, stream);
+}
+
+// Times every (lanes per location, warps per CTA) shape on the caller's problem and
+// records the fastest for this block size and kind of evaluation.
+int autotune(Plan* p, const double* y_dev, const double* theta, bool grad, int* G_out, int* W_out,
+             cudaStream_t stream) {
+  if (!p || !y_dev || !theta_ok(theta)) return VECCHIA_EINVAL;
+  const int K = p->m + 1;
+  int dev = 0;
+  VECCHIA_CUDA_TRY(cudaGetDevice(&dev));
+  double* out = nullptr;
+  if (cudaMalloc(&out, sizeof(double) * 4) != cudaSuccess) return VECCHIA_ENOMEM;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  int bestG = default_lanes(K), bestW = 0, rc = VECCHIA_OK;
+  for (int G : {8, 16, 32}) {
+    for (int W : {12, 11, 10, 9, 8, 6, 4}) {
+      LaunchCfg cfg;
+      if (shape_for(K, grad, G, W, &cfg) != VECCHIA_OK) continue;
+      float tmin = 1e30f;
+      for (int rep = 0; rep < 3 && !rc; ++rep) {
+        cudaEventRecord(e0, stream);
+        rc = launch_with(p, y_dev, theta, grad, cfg, out, nullptr, stream);
+        cudaEventRecord(e1, stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) rc = VECCHIA_ECUDA;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0) tmin = std::min(tmin, ms);
+      }
+      if (rc) break;
+      if (tmin < best) {
+        best = tmin;
+        bestG = G;
+        bestW = W;
+      }
+    }
+    if (rc) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(out);
+  if (rc) return rc;
+  set_tuned(dev, K, grad, bestG, bestW);
+  if (G_out) *G_out = bestG;
+  if (W_out) *W_out = bestW;
   return VECCHIA_OK;
 }
 
@@ -261,7 +400,7 @@ extern "C" int vecchia_loglik_noalloc(const double* xy_dev, const double* y_dev,
   a.partial = partial;
   a.terms = nullptr;
   a.errloc = errloc;
-  vecchia_lik_kernel<false><<<cfg.blocks, cfg.W * 32, cfg.smem, s>>>(a);
+  launch_lik(cfg, false, a, s);
   VECCHIA_CUDA_TRY(cudaGetLastError());
   vecchia_finalize_kernel<<<1, 32, 0, s>>>(partial, nw, theta[0], theta[1], theta[3], 0, out_dev);
   VECCHIA_CUDA_TRY(cudaGetLastError());

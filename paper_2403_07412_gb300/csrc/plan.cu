@@ -382,6 +382,8 @@ static void plan_free(Plan* p) {
 int launch_loglik(Plan* p, const double* y_dev, const double* theta, bool grad, double* out_dev,
                   double* terms_dev, cudaStream_t stream);
 void forget_plan_in_batches(const void* plan);
+int autotune(Plan* p, const double* y_dev, const double* theta, bool grad, int* G_out, int* W_out,
+             cudaStream_t stream);
 
 }  // namespace vecchia
 
@@ -497,6 +499,16 @@ int vecchia_loglik_terms(vecchia_plan_t plan, const double* y_dev, const double 
                          double* terms_dev, void* stream) {
   if (!terms_dev) return VECCHIA_EINVAL;
   return vecchia::launch_loglik(plan, y_dev, theta, want_grad != 0, nullptr, terms_dev, (cudaStream_t)stream);
+}
+
+int vecchia_autotune(vecchia_plan_t plan, const double* y_dev, const double theta[4], int want_grad,
+                     int32_t* lanes_out, int32_t* warps_out, void* stream) {
+  int G = 0, W = 0;
+  const int rc = vecchia::autotune(plan, y_dev, theta, want_grad != 0, &G, &W, (cudaStream_t)stream);
+  if (rc) return rc;
+  if (lanes_out) *lanes_out = G;
+  if (warps_out) *warps_out = W;
+  return VECCHIA_OK;
 }
 
 int vecchia_last_error_location(vecchia_plan_t plan, int64_t* loc) {

@@ -52,6 +52,8 @@ SIGNATURES = {
     "vecchia_fp64_peak": (ctypes.c_int, [_dp, _vp]),
     "vecchia_loglik_noalloc": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i64, _i32, _dp, _vp, _vp]),
     "vecchia_batched_prepare": (ctypes.c_int, [_dp, _i32, _vp]),
+    "vecchia_autotune": (ctypes.c_int, [_vp, _vp, _dp, ctypes.c_int, ctypes.POINTER(_i32), ctypes.POINTER(_i32),
+                                        _vp]),
     "vecchia_loglik_batched": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i32, _vp, _i32,
                                               ctypes.c_int, _vp, _vp]),
 }
@@ -217,6 +219,15 @@ def vecchia_loglik_noalloc(xy: torch.Tensor, y: torch.Tensor, nbr: torch.Tensor,
                                       _vp(_stream(stream)))
     _check(rc, "vecchia_loglik_noalloc")
     return out
+
+
+def vecchia_autotune(plan: Plan, y: torch.Tensor, theta, want_grad: bool = True, stream=None):
+    """Time the launch shapes for this plan's block size; returns (lanes per location, warps per CTA)."""
+    y = _dev_f64(y, plan.n, "y")
+    g, w = _i32(0), _i32(0)
+    _check(lib().vecchia_autotune(plan.handle, _vp(y.data_ptr()), _theta(theta), 1 if want_grad else 0,
+                                  ctypes.byref(g), ctypes.byref(w), _vp(_stream(stream))), "vecchia_autotune")
+    return int(g.value), int(w.value)
 
 
 def vecchia_batched_prepare(nus, stream=None) -> None:

@@ -311,3 +311,43 @@ def test_autograd_function(V):
     lp = oracle.vecchia(xy[perm], y[perm], 15, (1.2, 0.07, 1.5 + h, 0.03))
     lm = oracle.vecchia(xy[perm], y[perm], 15, (1.2, 0.07, 1.5 - h, 0.03))
     assert abs(th.grad.numpy()[2] - (lp - lm) / (2 * h)) <= 1e-5 * abs((lp - lm) / (2 * h)) + 1e-6
+
+
+@pytest.mark.parametrize("lanes", [8, 16, 32])
+@pytest.mark.parametrize("m", [10, 30, 63])
+def test_lanes_per_location_shapes_match_oracle(V, lanes, m, monkeypatch):
+    # Every launch shape (32/lanes locations per warp) gives the oracle's terms, including
+    # the ragged last round of locations and the short early conditioning sets.
+    monkeypatch.setenv("VECCHIA_LANES_PER_LOCATION", str(lanes))
+    n = 1531
+    theta = (1.1, 0.06, 1.5, 0.03)
+    xy = datagen.gmm_locations(n, 40 + m)
+    y = datagen.field_rff(xy, theta, 41 + m, features=512)
+    perm = oracle.order_random(n, 42 + m)
+    p = _plan_given(V, xy, m, perm)
+    yd = _dev(y)
+    want = oracle.vecchia_rows(xy[perm], y[perm], m, theta, want_grad=True)
+    _check_terms(V.vecchia_loglik_terms(p, yd, theta, want_grad=True).cpu().numpy(), want, grad=True)
+    _check_terms(V.vecchia_loglik_terms(p, yd, theta).cpu().numpy(), want[:, 0])
+    tot = V.vecchia_loglik_grad(p, yd, theta).cpu().numpy()
+    ref = oracle.compensated_sum(want)
+    assert abs(tot[0] - ref[0]) <= W.LOGLIK_RTOL * np.abs(want[:, 0]).sum()
+    for k in (1, 2, 3):
+        assert abs(tot[k] - ref[k]) <= W.GRAD_RTOL * np.abs(want[:, k]).sum()
+
+
+def test_autotune_records_a_shape(V):
+    xy = datagen.uniform_locations(20_000, 50)
+    theta = (1.0, 0.05, 1.0, 0.02)
+    y = datagen.field_rff(xy, theta, 51, features=512)
+    p = V.Plan(xy, 30)
+    yd = _dev(y)
+    before = V.vecchia_loglik_grad(p, yd, theta).cpu().numpy()
+    g, w = V.vecchia_autotune(p, yd, theta, want_grad=True)
+    assert g in (8, 16, 32) and 1 <= w <= 12
+    after = V.vecchia_loglik_grad(p, yd, theta).cpu().numpy()
+    terms = V.vecchia_loglik_terms(p, yd, theta, want_grad=True).cpu().numpy()
+    den = np.abs(terms).sum(axis=0)
+    assert abs(after[0] - before[0]) <= W.LOGLIK_RTOL * den[0]
+    for k in (1, 2, 3):
+        assert abs(after[k] - before[k]) <= W.GRAD_RTOL * den[k]
