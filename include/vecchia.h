@@ -52,7 +52,8 @@ enum {
 enum {
   VECCHIA_ORDER_GIVEN = 0,  /* use perm_in                                          */
   VECCHIA_ORDER_RANDOM = 1, /* Sec. V-A random ordering (splitmix64 Fisher–Yates)   */
-  VECCHIA_ORDER_MAXMIN = 2  /* Sec. V-A maxmin ordering (exact greedy farthest point) */
+  VECCHIA_ORDER_MAXMIN = 2, /* Sec. V-A maxmin ordering (exact greedy farthest point) */
+  VECCHIA_ORDER_MORTON = 3  /* Sec. V-A Morton (Z-order) ordering                     */
 };
 
 /* Largest conditioning-set size m accepted by the likelihood kernels. */
@@ -69,7 +70,10 @@ enum {
  *             j = splitmix64() mod (i+1)), splitmix64 state initialised to `seed`.
  *             MAXMIN: first the point nearest the centroid, then repeatedly the point
  *             whose minimum squared distance to those chosen is largest; ties to the
- *             lowest original index.  GIVEN: perm_in.
+ *             lowest original index.  MORTON: each coordinate mapped to a 16-bit cell
+ *             q = min(65535, floor((v - lo)/(hi - lo) * 65536)) over the bounding box,
+ *             bits interleaved (x in the even bits), sorted by (code, original index).
+ *             GIVEN: perm_in.
  *   perm_in : n int64 (host), a permutation of 0..n-1, perm_in[k] = original index of
  *             the k-th ordered location; only read for ORDER_GIVEN (else may be NULL).
  *   stream  : stream for the GPU neighbour search and uploads.

@@ -9,9 +9,10 @@ What each function follows:
 
 * :func:`matern` — Eq. (2) (Sec. IV-A), through ``std::cyl_bessel_k``.
 * :func:`loglik_exact` — Eq. (1), dense, with the oracle's own Cholesky.
-* :func:`order_random` / :func:`order_maxmin` — Sec. V-A orderings
-  (random = splitmix64-driven Fisher–Yates; maxmin = greedy farthest point
-  from the point nearest the centroid, ties to the lowest index).
+* :func:`order_random` / :func:`order_maxmin` / :func:`order_morton` — Sec. V-A
+  orderings (random = splitmix64-driven Fisher–Yates; maxmin = greedy farthest
+  point from the point nearest the centroid, ties to the lowest index; Morton =
+  Z-order of 16-bit cell indices).
 * :func:`knn_rows` — Algorithm 1, nearest-neighbour loop: the m nearest
   *previously ordered* points, ties by index, brute force.
 * :func:`vecchia_rows` / :func:`vecchia` — Sec. V-B: the Vecchia product of
@@ -70,6 +71,7 @@ def _load():
             "oracle_splitmix64": (None, [c_u64, c_i64, _u64p]),
             "oracle_order_random": (c_int, [c_i64, c_u64, _i64p]),
             "oracle_order_maxmin": (c_int, [c_i64, _dp, _i64p]),
+            "oracle_order_morton": (c_int, [c_i64, _dp, _i64p]),
             "oracle_knn_rows": (c_int, [c_i64, _dp, c_i32, _i64p, c_i64, _i32p]),
             "oracle_vecchia_rows": (c_int, [c_i64, _dp, _dp, c_i32, _dp, _i64p, c_i64, _i32p, c_int,
                                             _dp, _dp, _i64p]),
@@ -143,6 +145,14 @@ def order_maxmin(xy) -> np.ndarray:
     xy = _f64(xy).reshape(-1, 2)
     perm = np.empty(xy.shape[0], dtype=np.int64)
     _load().oracle_order_maxmin(xy.shape[0], _p(xy, _dp), _p(perm, _i64p))
+    return perm
+
+
+def order_morton(xy) -> np.ndarray:
+    """Morton (Z-order) ordering of 16-bit cell indices over the bounding box."""
+    xy = _f64(xy).reshape(-1, 2)
+    perm = np.empty(xy.shape[0], dtype=np.int64)
+    _load().oracle_order_morton(xy.shape[0], _p(xy, _dp), _p(perm, _i64p))
     return perm
 
 

@@ -338,6 +338,35 @@ int oracle_order_maxmin(int64_t n, const double* xy, int64_t* perm) {
   return 0;
 }
 
+// Morton ordering (Sec. V-A and Fig. 1, the Z-order alternative to random ordering):
+// a 16-bit cell index per coordinate over the bounding box,
+// q = min(65535, floor((v - lo)/(hi - lo) * 65536)), q = 0 if hi == lo; the Z-order key
+// takes bit b of x to position 2b and bit b of y to position 2b+1; sort by (key, index).
+int oracle_order_morton(int64_t n, const double* xy, int64_t* perm) {
+  if (n <= 0) return 0;
+  double lo[2] = {xy[0], xy[1]}, hi[2] = {xy[0], xy[1]};
+  for (int64_t i = 0; i < n; ++i)
+    for (int a = 0; a < 2; ++a) {
+      lo[a] = std::min(lo[a], xy[2 * i + a]);
+      hi[a] = std::max(hi[a], xy[2 * i + a]);
+    }
+  std::vector<uint64_t> key(n);
+  for (int64_t i = 0; i < n; ++i) {
+    uint64_t q[2];
+    for (int a = 0; a < 2; ++a) {
+      if (!(hi[a] > lo[a])) { q[a] = 0; continue; }
+      const double f = std::floor((xy[2 * i + a] - lo[a]) / (hi[a] - lo[a]) * 65536.0);
+      q[a] = f < 0.0 ? 0 : (f > 65535.0 ? 65535 : (uint64_t)f);
+    }
+    uint64_t k = 0;
+    for (int bit = 15; bit >= 0; --bit) k = (k << 2) | (((q[1] >> bit) & 1) << 1) | ((q[0] >> bit) & 1);
+    key[i] = (k << 32) | (uint64_t)i;  // n < 2^32 here
+  }
+  std::sort(key.begin(), key.end());
+  for (int64_t i = 0; i < n; ++i) perm[i] = (int64_t)(key[i] & 0xFFFFFFFFULL);
+  return 0;
+}
+
 // Brute-force conditioning sets for the listed ordered rows (Algorithm 1, lines
 // on the nearest-neighbour loop).  xy is ordered; out is nrows x m, -1 padded.
 int oracle_knn_rows(int64_t n, const double* xy, int32_t m, const int64_t* rows, int64_t nrows,

@@ -306,12 +306,12 @@ __device__ __forceinline__ void process_location(int64_t i, bool active, const F
       A[oj + r - j] = tv * inv;
     }
     __syncwarp();
-    // Trailing update of the prefix [1, oj).  Full batches of four slots per lane are
+    // Trailing update of the prefix [1, oj).  Full batches of eight slots per lane are
     // software-pipelined (the next batch's shared-memory loads are issued before this
     // batch's results are stored); the remainder runs one slot at a time, so no FP64
     // instruction is issued for a slot that no lane owns.
     const double* Lc = A + oj - j;  // Lc[r] = L[r][j]
-    constexpr int U = 4;
+    constexpr int U = 8;
     const int nfull = (oj - 1) / (G * U);
     const int tail0 = 1 + G * U * nfull;
     if (nfull > 0) {

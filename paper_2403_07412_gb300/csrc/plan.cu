@@ -6,7 +6,8 @@
 //            Flood 2014), j = next() mod (i+1) for i = n-1 .. 1;
 //   maxmin — exact greedy farthest-point ordering from the point nearest the centroid,
 //            ties to the lowest original index; a lazy max-heap of each point's squared
-//            distance to the chosen set, updated only inside the disc that can change.
+//            distance to the chosen set, updated only inside the disc that can change;
+//   morton — Z-order of 16-bit cell indices over the bounding box.
 // Conditioning sets are found on the GPU, one thread per ordered location, over a
 // hierarchy of uniform grids: level l holds the first N_l ordered points (N_l doubling),
 // bucketed by cell with each cell's points in ascending ordered index, so a query i
@@ -41,6 +42,34 @@ static void order_random(int64_t n, uint64_t seed, int64_t* perm) {
     const int64_t j = (int64_t)(splitmix64(st) % (uint64_t)(i + 1));
     std::swap(perm[i], perm[j]);
   }
+}
+
+// Morton (Z-order) ordering (Sec. V-A, Fig. 1): each coordinate is mapped to a 16-bit
+// cell index over the bounding box, q = min(65535, floor((v - lo) / (hi - lo) * 65536))
+// (q = 0 when hi == lo), the two indices are bit-interleaved (x in the even bits), and
+// locations are sorted by (code, original index).
+static uint32_t morton_cell(double v, double lo, double hi) {
+  if (!(hi > lo)) return 0;
+  const double t = (v - lo) / (hi - lo);
+  const double q = std::floor(t * 65536.0);
+  return q < 0.0 ? 0u : (q > 65535.0 ? 65535u : (uint32_t)q);
+}
+
+static void order_morton(int64_t n, const double* xy, int64_t* perm) {
+  double x0 = xy[0], x1 = xy[0], y0 = xy[1], y1 = xy[1];
+  for (int64_t i = 1; i < n; ++i) {
+    x0 = std::min(x0, xy[2 * i]); x1 = std::max(x1, xy[2 * i]);
+    y0 = std::min(y0, xy[2 * i + 1]); y1 = std::max(y1, xy[2 * i + 1]);
+  }
+  std::vector<std::pair<uint32_t, int64_t>> key(n);
+  for (int64_t i = 0; i < n; ++i) {
+    const uint32_t qx = morton_cell(xy[2 * i], x0, x1), qy = morton_cell(xy[2 * i + 1], y0, y1);
+    uint32_t code = 0;
+    for (int b = 0; b < 16; ++b) code |= ((qx >> b) & 1u) << (2 * b) | ((qy >> b) & 1u) << (2 * b + 1);
+    key[i] = {code, i};
+  }
+  std::sort(key.begin(), key.end());
+  for (int64_t k = 0; k < n; ++k) perm[k] = key[k].second;
 }
 
 // Squared distance without contraction: the host compiler runs with -ffp-contract=off.
@@ -397,7 +426,8 @@ int vecchia_plan_create(const double* xy_host, int64_t n, int32_t m, int order, 
   if (!out) return VECCHIA_EINVAL;
   *out = nullptr;
   if (!xy_host || n < 1 || n > 2147483647LL || m < 1 || m > kMaxM) return VECCHIA_EINVAL;
-  if (order != VECCHIA_ORDER_GIVEN && order != VECCHIA_ORDER_RANDOM && order != VECCHIA_ORDER_MAXMIN)
+  if (order != VECCHIA_ORDER_GIVEN && order != VECCHIA_ORDER_RANDOM && order != VECCHIA_ORDER_MAXMIN &&
+      order != VECCHIA_ORDER_MORTON)
     return VECCHIA_EINVAL;
   for (int64_t i = 0; i < 2 * n; ++i)
     if (!std::isfinite(xy_host[i])) return VECCHIA_EINVAL;
@@ -419,8 +449,10 @@ int vecchia_plan_create(const double* xy_host, int64_t n, int32_t m, int order, 
     }
   } else if (order == VECCHIA_ORDER_RANDOM) {
     order_random(n, seed, p->h_perm);
-  } else {
+  } else if (order == VECCHIA_ORDER_MAXMIN) {
     order_maxmin(n, xy_host, p->h_perm);
+  } else {
+    order_morton(n, xy_host, p->h_perm);
   }
   cudaStream_t s = (cudaStream_t)stream;
   int rc = VECCHIA_OK;

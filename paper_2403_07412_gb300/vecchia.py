@@ -24,7 +24,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libvecchia.so")
 
 OK, EINVAL, ENOTPD, ECUDA, ETIMEOUT, ENOMEM = range(6)
-ORDER_GIVEN, ORDER_RANDOM, ORDER_MAXMIN = 0, 1, 2
+ORDER_GIVEN, ORDER_RANDOM, ORDER_MAXMIN, ORDER_MORTON = 0, 1, 2, 3
 MAX_M = 63
 
 _lock = threading.Lock()

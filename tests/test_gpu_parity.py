@@ -102,6 +102,13 @@ def test_maxmin_ordering_bit_exact(V, kind, n):
     np.testing.assert_array_equal(p.perm(), oracle.order_maxmin(xy))
 
 
+@pytest.mark.parametrize("kind", ["uniform", "gmm"])
+def test_morton_ordering_bit_exact(V, kind):
+    xy = datagen.uniform_locations(30_000, 7) if kind == "uniform" else datagen.gmm_locations(30_000, 8)
+    p = V.Plan(xy, 10, order=V.ORDER_MORTON)
+    np.testing.assert_array_equal(p.perm(), oracle.order_morton(xy))
+
+
 @pytest.mark.parametrize("n,m,kind", [(2000, 10, "uniform"), (5000, 63, "gmm"), (7, 10, "uniform"),
                                       (1, 3, "uniform"), (3000, 30, "dups"), (40_000, 60, "gmm")])
 def test_knn_bit_exact(V, n, m, kind):

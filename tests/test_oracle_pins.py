@@ -148,6 +148,27 @@ def test_order_maxmin_property(oracle_mod):
         assert dk[0] == dk.max()
 
 
+def test_order_morton_z_pattern(oracle_mod):
+    # 4x4 grid (x fastest): the Z-order visits 2x2 quads in Z order, each quad in Z order.
+    g = np.array([[x, y] for y in (0.0, 1 / 3, 2 / 3, 1.0) for x in (0.0, 1 / 3, 2 / 3, 1.0)])
+    want = [0, 1, 4, 5, 2, 3, 6, 7, 8, 9, 12, 13, 10, 11, 14, 15]
+    assert oracle_mod.order_morton(g).tolist() == want
+    # duplicates keep their original order; a degenerate (constant) axis maps to cell 0
+    pts = np.array([[0.5, 0.2], [0.5, 0.9], [0.5, 0.2], [0.5, 0.0]])
+    assert oracle_mod.order_morton(pts).tolist() == [3, 0, 2, 1]
+
+
+def test_order_morton_matches_sorting_by_interleaved_key(oracle_mod):
+    xy = datagen.gmm_locations(3000, 9)
+    lo, hi = xy.min(0), xy.max(0)
+    q = np.minimum(np.floor((xy - lo) / (hi - lo) * 65536.0), 65535).astype(np.int64)
+    key = np.zeros(len(xy), dtype=np.int64)
+    for b in range(16):
+        key |= ((q[:, 0] >> b) & 1) << (2 * b)
+        key |= ((q[:, 1] >> b) & 1) << (2 * b + 1)
+    np.testing.assert_array_equal(oracle_mod.order_morton(xy), np.lexsort((np.arange(len(xy)), key)))
+
+
 # ----------------------------------------------------------------- kNN
 def test_knn_against_numpy_brute_force(oracle_mod):
     xy = datagen.uniform_locations(700, 3)
