@@ -56,6 +56,11 @@ enum {
   VECCHIA_ORDER_MORTON = 3  /* Sec. V-A Morton (Z-order) ordering                     */
 };
 
+enum {
+  VECCHIA_KERNEL_MATERN = 0, /* Eq. (2): sigma2 2^{1-nu}/Gamma(nu) (d/beta)^nu K_nu(d/beta)       */
+  VECCHIA_KERNEL_POWEXP = 1  /* Eq. (3): sigma2 exp(-d^nu / beta), 0 < nu <= 2 (nu = the exponent) */
+};
+
 /* Largest conditioning-set size m accepted by the likelihood kernels. */
 #define VECCHIA_MAX_M 63
 
@@ -88,6 +93,17 @@ int vecchia_plan_create(const double* xy_host, int64_t n, int32_t m, int order, 
 
 /* Frees every device and host resource of the plan (NULL is ignored). */
 void vecchia_plan_destroy(vecchia_plan_t plan);
+
+/*
+ * vecchia_plan_set_kernel — the covariance family used by this plan's likelihood calls:
+ * VECCHIA_KERNEL_MATERN (default, Eq. (2)) or VECCHIA_KERNEL_POWEXP (the power
+ * exponential of Eq. (3), used by the paper for its real data, Sec. VI-C).  With the
+ * power exponential, theta = {sigma2, beta, nu, tau2} means C(d) = sigma2 exp(-d^nu/beta)
+ * + tau2 [d = 0 on the diagonal] and requires 0 < nu <= 2 (EINVAL otherwise); the
+ * gradient is still d/d(sigma2, beta, tau2).  Not for plans in use on a stream.  The
+ * batched call accepts Matérn plans only.  Errors: EINVAL.
+ */
+int vecchia_plan_set_kernel(vecchia_plan_t plan, int kernel);
 
 /* n and m of the plan. */
 int vecchia_plan_size(vecchia_plan_t plan, int64_t* n, int32_t* m);
@@ -143,6 +159,15 @@ int vecchia_loglik_terms(vecchia_plan_t plan, const double* y_dev, const double 
  */
 int vecchia_matern(const double* d_dev, int64_t count, const double theta[4], double* c_dev,
                    double* dcdbeta_dev, void* stream);
+
+/*
+ * vecchia_covariance — vecchia_matern for either covariance family (VECCHIA_KERNEL_*):
+ * C(d) of Eq. (2) or Eq. (3) and dC/dbeta, through the kernels' device code.  Same
+ * arguments and errors as vecchia_matern, plus EINVAL for an unknown kernel or, for the
+ * power exponential, an exponent outside (0, 2].
+ */
+int vecchia_covariance(int kernel, const double* d_dev, int64_t count, const double theta[4], double* c_dev,
+                       double* dcdbeta_dev, void* stream);
 
 /*
  * vecchia_batched_prepare — builds the covariance tables the batched call may use, one per

@@ -7,7 +7,8 @@ with the CUDA library.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
 
 What each function follows:
 
-* :func:`matern` — Eq. (2) (Sec. IV-A), through ``std::cyl_bessel_k``.
+* :func:`matern` — Eq. (2) (Sec. IV-A), through ``std::cyl_bessel_k``;
+  :func:`powexp` — Eq. (3), the power-exponential family of the real-data model.
 * :func:`loglik_exact` — Eq. (1), dense, with the oracle's own Cholesky.
 * :func:`order_random` / :func:`order_maxmin` / :func:`order_morton` — Sec. V-A
   orderings (random = splitmix64-driven Fisher–Yates; maxmin = greedy farthest
@@ -68,15 +69,17 @@ def _load():
             "oracle_matern": (c_int, [c_i64, _dp, c_d, c_d, c_d, _dp]),
             "oracle_matern_dbeta": (c_int, [c_i64, _dp, c_d, c_d, c_d, _dp]),
             "oracle_bessel_k": (c_int, [c_i64, _dp, c_d, _dp]),
+            "oracle_powexp": (c_int, [c_i64, _dp, c_d, c_d, c_d, _dp]),
+            "oracle_powexp_dbeta": (c_int, [c_i64, _dp, c_d, c_d, c_d, _dp]),
             "oracle_splitmix64": (None, [c_u64, c_i64, _u64p]),
             "oracle_order_random": (c_int, [c_i64, c_u64, _i64p]),
             "oracle_order_maxmin": (c_int, [c_i64, _dp, _i64p]),
             "oracle_order_morton": (c_int, [c_i64, _dp, _i64p]),
             "oracle_knn_rows": (c_int, [c_i64, _dp, c_i32, _i64p, c_i64, _i32p]),
             "oracle_vecchia_rows": (c_int, [c_i64, _dp, _dp, c_i32, _dp, _i64p, c_i64, _i32p, c_int,
-                                            _dp, _dp, _i64p]),
+                                            _dp, _dp, _i64p, c_int]),
             "oracle_sum_columns": (None, [c_i64, c_i32, _dp, _dp]),
-            "oracle_loglik_exact": (c_int, [c_i64, _dp, _dp, _dp, _dp, _dp]),
+            "oracle_loglik_exact": (c_int, [c_i64, _dp, _dp, _dp, _dp, _dp, c_int]),
             "oracle_block_logdensity": (c_int, [c_i32, _dp, _dp, _dp]),
         }
         for name, (res, args) in sig.items():
@@ -116,6 +119,22 @@ def matern_dbeta(d, sigma2: float, beta: float, nu: float) -> np.ndarray:
     d = _f64(np.atleast_1d(d))
     out = np.empty_like(d)
     _load().oracle_matern_dbeta(d.size, _p(d, _dp), sigma2, beta, nu, _p(out, _dp))
+    return out
+
+
+def powexp(d, sigma2: float, beta: float, alpha: float) -> np.ndarray:
+    """Eq. (3) covariance sigma2 exp(-d^alpha / beta) at distances ``d``."""
+    d = _f64(np.atleast_1d(d))
+    out = np.empty_like(d)
+    _load().oracle_powexp(d.size, _p(d, _dp), sigma2, beta, alpha, _p(out, _dp))
+    return out
+
+
+def powexp_dbeta(d, sigma2: float, beta: float, alpha: float) -> np.ndarray:
+    """dC/dbeta of Eq. (3)."""
+    d = _f64(np.atleast_1d(d))
+    out = np.empty_like(d)
+    _load().oracle_powexp_dbeta(d.size, _p(d, _dp), sigma2, beta, alpha, _p(out, _dp))
     return out
 
 
@@ -175,10 +194,11 @@ class OracleNotPD(RuntimeError):
 
 
 def vecchia_rows(xy_ordered, y_ordered, m: int, theta, rows=None, nbr=None, want_grad=False,
-                 return_mu_s=False):
+                 return_mu_s=False, family=0):
     """Per-location Vecchia terms (and gradients) for the given ordered rows.
 
-    theta = (sigma2, beta, nu, tau2).  Returns an array of shape (nrows,) or
+    theta = (sigma2, beta, nu, tau2); family 0 = Matérn (Eq. 2), 1 = power exponential
+    (Eq. 3, nu = exponent).  Returns an array of shape (nrows,) or
     (nrows, 4) = (l_i, dl_i/dsigma2, dl_i/dbeta, dl_i/dtau2).
     """
     xy = _f64(xy_ordered).reshape(-1, 2)
@@ -195,7 +215,7 @@ def vecchia_rows(xy_ordered, y_ordered, m: int, theta, rows=None, nbr=None, want
     bad = np.full(1, -1, dtype=np.int64)
     rc = _load().oracle_vecchia_rows(n, _p(xy, _dp), _p(y, _dp), m, _p(th, _dp), _p(rows, _i64p),
                                      rows.size, _p(nbr, _i32p), 1 if want_grad else 0, _p(out, _dp),
-                                     _p(mu_s, _dp), _p(bad, _i64p))
+                                     _p(mu_s, _dp), _p(bad, _i64p), int(family))
     if rc:
         raise OracleNotPD(int(bad[0]))
     res = out if want_grad else out[:, 0]
@@ -212,14 +232,14 @@ def compensated_sum(v) -> np.ndarray:
     return out
 
 
-def vecchia(xy_ordered, y_ordered, m: int, theta, want_grad=False):
+def vecchia(xy_ordered, y_ordered, m: int, theta, want_grad=False, family=0):
     """Vecchia log-likelihood over all ordered locations: l or (l, dsigma2, dbeta, dtau2)."""
-    terms = vecchia_rows(xy_ordered, y_ordered, m, theta, want_grad=want_grad)
+    terms = vecchia_rows(xy_ordered, y_ordered, m, theta, want_grad=want_grad, family=family)
     s = compensated_sum(terms)
     return s if want_grad else float(s[0])
 
 
-def loglik_exact(xy, y, theta, want_grad=False):
+def loglik_exact(xy, y, theta, want_grad=False, family=0):
     """Eq. (1): exact zero-mean Gaussian log-likelihood (dense, O(n^3))."""
     xy = _f64(xy).reshape(-1, 2)
     y = _f64(y)
@@ -227,7 +247,7 @@ def loglik_exact(xy, y, theta, want_grad=False):
     out = np.empty(1)
     g = np.empty(3)
     rc = _load().oracle_loglik_exact(xy.shape[0], _p(xy, _dp), _p(y, _dp), _p(th, _dp), _p(out, _dp),
-                                     _p(g, _dp) if want_grad else None)
+                                     _p(g, _dp) if want_grad else None, int(family))
     if rc:
         raise OracleNotPD(-1)
     return (float(out[0]), g) if want_grad else float(out[0])

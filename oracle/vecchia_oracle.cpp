@@ -10,6 +10,7 @@
 // Every function cites the passage it follows:
 //   Eq. (1)  exact Gaussian log-likelihood                       (Sec. IV-A)
 //   Eq. (2)  Matérn covariance, theta = (sigma^2, beta, nu)      (Sec. IV-A)
+//   Eq. (3)  power-exponential covariance (real-data model, Sec. VI-C)
 //   Vecchia factorisation p(y1) prod p(y_i | y_{J_i})             (Sec. V-B)
 //   Algorithm 1: permutation, m nearest previously-ordered
 //   neighbours, conditional mean / variance, univariate terms     (Sec. V-B)
@@ -56,6 +57,26 @@ double matern_dbeta(double d, double sigma2, double beta, double nu) {
   const double k = std::cyl_bessel_k(std::fabs(nu - 1.0), x);
   if (k == 0.0) return 0.0;
   return sigma2 * std::pow(2.0, 1.0 - nu) / std::tgamma(nu) * std::pow(x, nu + 1.0) * k / beta;
+}
+
+// Eq. (3), the power-exponential covariance: C(d) = sigma2 exp(-d^nu / beta), and
+// dC/dbeta = sigma2 exp(-d^nu/beta) d^nu / beta^2 (here nu is the exponent alpha).
+double powexp(double d, double sigma2, double beta, double nu) {
+  return sigma2 * std::exp(-std::pow(d, nu) / beta);
+}
+
+double powexp_dbeta(double d, double sigma2, double beta, double nu) {
+  const double a = std::pow(d, nu);
+  return sigma2 * std::exp(-a / beta) * a / (beta * beta);
+}
+
+// Covariance family 0 = Matérn (Eq. 2), 1 = power exponential (Eq. 3).
+double cov(int family, double d, double sigma2, double beta, double nu) {
+  return family == 1 ? powexp(d, sigma2, beta, nu) : matern(d, sigma2, beta, nu);
+}
+
+double cov_dbeta(int family, double d, double sigma2, double beta, double nu) {
+  return family == 1 ? powexp_dbeta(d, sigma2, beta, nu) : matern_dbeta(d, sigma2, beta, nu);
 }
 
 // Squared Euclidean distance, evaluated as round(round(dx*dx) + round(dy*dy)).
@@ -159,7 +180,7 @@ void knn_row(const double* xy, int64_t i, int m, int32_t* out) {
 //   d log N(y; 0, S)/d theta_p = -1/2 tr(S^{-1} S_p) + 1/2 a^T S_p a,  a = S^{-1} y,
 // with S_sigma2 = (S - tau2 I)/sigma2, S_tau2 = I, S_beta = [dC/dbeta(d_pq)].
 int location_term(const double* xy, const double* y, int64_t i, const int32_t* J, int mi,
-                  const double* theta, double* term, double* grad, double* mu_out, double* s_out) {
+                  const double* theta, int family, double* term, double* grad, double* mu_out, double* s_out) {
   const double sigma2 = theta[0], beta = theta[1], nu = theta[2], tau2 = theta[3];
   const int k = mi + 1;  // block B = J followed by i
   std::vector<int64_t> idx(k);
@@ -169,8 +190,8 @@ int location_term(const double* xy, const double* y, int64_t i, const int32_t* J
   for (int p = 0; p < k; ++p) {
     for (int q = 0; q < k; ++q) {
       const double d = std::sqrt(dist2(xy + 2 * idx[p], xy + 2 * idx[q]));
-      S[(size_t)p * k + q] = (p == q ? sigma2 + tau2 : matern(d, sigma2, beta, nu));
-      if (grad) D[(size_t)p * k + q] = (p == q ? 0.0 : matern_dbeta(d, sigma2, beta, nu));
+      S[(size_t)p * k + q] = (p == q ? sigma2 + tau2 : cov(family, d, sigma2, beta, nu));
+      if (grad) D[(size_t)p * k + q] = (p == q ? 0.0 : cov_dbeta(family, d, sigma2, beta, nu));
     }
   }
   const double cii = S[(size_t)mi * k + mi];
@@ -265,6 +286,16 @@ int oracle_matern(int64_t n, const double* d, double sigma2, double beta, double
 
 int oracle_matern_dbeta(int64_t n, const double* d, double sigma2, double beta, double nu, double* out) {
   for (int64_t i = 0; i < n; ++i) out[i] = matern_dbeta(d[i], sigma2, beta, nu);
+  return 0;
+}
+
+int oracle_powexp(int64_t n, const double* d, double sigma2, double beta, double nu, double* out) {
+  for (int64_t i = 0; i < n; ++i) out[i] = powexp(d[i], sigma2, beta, nu);
+  return 0;
+}
+
+int oracle_powexp_dbeta(int64_t n, const double* d, double sigma2, double beta, double nu, double* out) {
+  for (int64_t i = 0; i < n; ++i) out[i] = powexp_dbeta(d[i], sigma2, beta, nu);
   return 0;
 }
 
@@ -385,7 +416,7 @@ int oracle_knn_rows(int64_t n, const double* xy, int32_t m, const int64_t* rows,
 // bad_row (optional): first failing row index on a non-PD block.
 int oracle_vecchia_rows(int64_t n, const double* xy, const double* y, int32_t m, const double* theta,
                         const int64_t* rows, int64_t nrows, const int32_t* nbr, int want_grad,
-                        double* out, double* mu_s, int64_t* bad_row) {
+                        double* out, double* mu_s, int64_t* bad_row, int family) {
   (void)n;
   const int w = want_grad ? 4 : 1;
   int64_t first_bad = -1;
@@ -396,7 +427,7 @@ int oracle_vecchia_rows(int64_t n, const double* xy, const double* y, int32_t m,
     while (mi < m && J[mi] >= 0) ++mi;
     double g[3];
     double mu = 0.0, s = 0.0;
-    const int rc = location_term(xy, y, rows[r], J, mi, theta, out + (size_t)r * w,
+    const int rc = location_term(xy, y, rows[r], J, mi, theta, family, out + (size_t)r * w,
                                  want_grad ? g : nullptr, &mu, &s);
     if (rc) {
 #pragma omp critical
@@ -423,14 +454,14 @@ void oracle_sum_columns(int64_t nrows, int32_t cols, const double* v, double* ou
 // tau2 delta_pq; O(n^3) with the oracle's own Cholesky.  grad (optional):
 // d l / d(sigma2, beta, tau2) by -1/2 tr(Sigma^{-1} Sigma_p) + 1/2 a^T Sigma_p a.
 int oracle_loglik_exact(int64_t n, const double* xy, const double* y, const double* theta,
-                        double* out, double* grad) {
+                        double* out, double* grad, int family) {
   const double sigma2 = theta[0], beta = theta[1], nu = theta[2], tau2 = theta[3];
   const int k = (int)n;
   std::vector<double> S((size_t)k * k), L((size_t)k * k), a(k);
   for (int p = 0; p < k; ++p)
     for (int q = 0; q < k; ++q) {
       const double d = std::sqrt(dist2(xy + 2 * p, xy + 2 * q));
-      S[(size_t)p * k + q] = p == q ? sigma2 + tau2 : matern(d, sigma2, beta, nu);
+      S[(size_t)p * k + q] = p == q ? sigma2 + tau2 : cov(family, d, sigma2, beta, nu);
     }
   if (!cholesky(k, S.data(), L.data())) return 2;
   chol_solve(k, L.data(), y, a.data());
@@ -448,7 +479,7 @@ int oracle_loglik_exact(int64_t n, const double* xy, const double* y, const doub
         if (t == 0) Sp = (S[(size_t)p * k + q] - (p == q ? tau2 : 0.0)) / sigma2;
         else if (t == 1) {
           const double d = std::sqrt(dist2(xy + 2 * p, xy + 2 * q));
-          Sp = p == q ? 0.0 : matern_dbeta(d, sigma2, beta, nu);
+          Sp = p == q ? 0.0 : cov_dbeta(family, d, sigma2, beta, nu);
         } else Sp = p == q ? 1.0 : 0.0;
         tr += Si[(size_t)q * k + p] * Sp;
         qd += a[p] * Sp * a[q];

@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(384) vecchia_batched_kernel(const BatchArgs a)
     }
     const MaternConst mc = load_matern_const(tab);
     ThetaConst tc;
-    tc.set(s2, beta, t2);
+    tc.set(s2, beta, t2, kFamilyMatern, nu);
     if (fd.lanes == 8) run_item<GRAD, 8>(fd, tile, smem, a, base, tab, mc, tc, out, lane);
     else if (fd.lanes == 16) run_item<GRAD, 16>(fd, tile, smem, a, base, tab, mc, tc, out, lane);
     else run_item<GRAD, 32>(fd, tile, smem, a, base, tab, mc, tc, out, lane);
@@ -382,7 +382,7 @@ extern "C" int vecchia_loglik_batched(const vecchia_plan_t* plans, const double*
   using namespace vecchia;
   if (!plans || !y_devs || nfields < 1 || ntheta < 1 || !thetas_dev || !out_dev) return VECCHIA_EINVAL;
   for (int f = 0; f < nfields; ++f)
-    if (!plans[f] || !y_devs[f]) return VECCHIA_EINVAL;
+    if (!plans[f] || !y_devs[f] || plans[f]->family != kFamilyMatern) return VECCHIA_EINVAL;
   want_grad = want_grad ? 1 : 0;
   int dev = 0;
   VECCHIA_CUDA_TRY(cudaGetDevice(&dev));

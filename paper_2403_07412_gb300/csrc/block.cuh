@@ -143,12 +143,17 @@ __device__ __forceinline__ void build_schedules(int K, uint16_t* sched, uint32_t
   }
 }
 
-// theta-dependent constants of one evaluation.
+// theta-dependent constants of one evaluation.  inv_len scales distances so that
+// u = (d inv_len)^2 is the table's variable: 1/beta for the Matérn, beta^(-1/alpha) for
+// the power exponential; dbeta_coef turns h = u rho'(u) into dC/dbeta / 1:
+// -2 sigma2 / beta (Matérn) or -2 sigma2 / (alpha beta) (power exponential).
 struct ThetaConst {
-  double sigma2, inv_beta, gamma1, inv_sigma2, tau2;
-  __device__ void set(double s2, double beta, double t2) {
+  double sigma2, inv_len, gamma1, inv_sigma2, tau2, dbeta_coef;
+  __device__ void set(double s2, double beta, double t2, int family, double nu) {
     sigma2 = s2;
-    inv_beta = 1.0 / beta;
+    const bool pe = family == kFamilyPowExp;
+    inv_len = pe ? exp(-log(beta) / nu) : 1.0 / beta;
+    dbeta_coef = -2.0 * s2 / (beta * (pe ? nu : 1.0));
     gamma1 = 1.0 + t2 / s2;
     inv_sigma2 = 1.0 / s2;
     tau2 = t2;
@@ -239,8 +244,8 @@ __device__ __forceinline__ void process_location(int64_t i, bool active, const F
       if (p < mi) {
         const int j = row[p];
         const double2 q = F.xy[j];
-        xv[s] = (q.x - ps.x) * tc.inv_beta;
-        yv[s] = (q.y - ps.y) * tc.inv_beta;
+        xv[s] = (q.x - ps.x) * tc.inv_len;
+        yv[s] = (q.y - ps.y) * tc.inv_len;
         fv = F.yf[j];
       }
       YV[p] = fv;
@@ -458,7 +463,7 @@ __device__ __forceinline__ void process_location(int64_t i, bool active, const F
     if (terms && active && sub == 0) {
       terms[0] = li;
       terms[1] = good ? (sS - tc.tau2 * tT) * tc.inv_sigma2 : nan;
-      terms[2] = good ? -2.0 * tc.sigma2 * tc.inv_beta * tB : nan;
+      terms[2] = good ? tc.dbeta_coef * tB : nan;
       terms[3] = good ? tT : nan;
     }
   }

@@ -31,9 +31,14 @@ constexpr size_t kTableBytes = sizeof(double) * (kNInt * kNDbl + kNConst) + size
 constexpr int kMaxM = VECCHIA_MAX_M;
 constexpr int kMaxK = kMaxM + 1;
 
+// Covariance families (VECCHIA_KERNEL_*): Matérn, Eq. (2); power exponential, Eq. (3).
+constexpr int kFamilyMatern = 0;
+constexpr int kFamilyPowExp = 1;
+
 struct Plan {
   int64_t n = 0;
   int32_t m = 0;
+  int family = kFamilyMatern;
   int device = 0;
   double* d_xy = nullptr;     // n x 2, original order
   int32_t* d_nbr = nullptr;   // n x m, ORIGINAL indices of J_i, -1 padded (ordered rows)

@@ -18,6 +18,8 @@
 namespace vecchia {
 
 int get_matern_table(double nu, cudaStream_t stream, const double** out);
+int get_cov_table(int family, double nu, cudaStream_t stream, const double** out);
+bool theta_ok_family(const double* th, int family);
 int launch_matern_table(double nu, double* tab, cudaStream_t stream);
 bool theta_ok(const double* th);
 
@@ -29,7 +31,8 @@ struct LikArgs {
   const double* __restrict__ tab;    // correlation table for nu
   int64_t n;
   int m;
-  double sigma2, beta, tau2;
+  int family;                        // kFamilyMatern or kFamilyPowExp
+  double sigma2, beta, nu, tau2;
   double* partial;                   // [nwarps][4]
   double* terms;                     // optional [n][1|4]
   unsigned long long* errloc;
@@ -64,7 +67,7 @@ __global__ void __launch_bounds__(384) vecchia_lik_kernel(const LikArgs a) {
 
   const MaternConst mc = load_matern_const(a.tab);
   ThetaConst tc;
-  tc.set(a.sigma2, a.beta, a.tau2);
+  tc.set(a.sigma2, a.beta, a.tau2, a.family, a.nu);
   FieldView F;
   F.xy = reinterpret_cast<const double2*>(a.xy);
   F.yf = a.yf;
@@ -88,8 +91,10 @@ __global__ void __launch_bounds__(384) vecchia_lik_kernel(const LikArgs a) {
 }
 
 // Deterministic reduction of the per-warp partials (fixed order, Neumaier).
+// Partials: [sum l_i, sum 1/2(r^2/s-1), sum beta pair sums, sum w^T g]; dbeta_div is 1
+// (Matérn) or alpha (power exponential).
 __global__ void vecchia_finalize_kernel(const double* __restrict__ partial, int64_t nw, double sigma2,
-                                        double beta, double tau2, int want_grad, double* out) {
+                                        double beta, double tau2, double dbeta_div, int want_grad, double* out) {
   if (threadIdx.x >= 4) return;
   const int k = threadIdx.x;
   Neumaier acc;
@@ -99,13 +104,12 @@ __global__ void vecchia_finalize_kernel(const double* __restrict__ partial, int6
     if (k == 0) out[0] = v;
     return;
   }
-  // Partials: [sum l_i, sum 1/2(r^2/s-1), sum beta pair sums, sum w^T g].
   __shared__ double sv[4];
   sv[k] = v;
   __syncwarp(0xFu);
   if (k == 0) out[0] = sv[0];
   if (k == 1) out[1] = (sv[1] - tau2 * sv[3]) / sigma2;
-  if (k == 2) out[2] = -2.0 * sigma2 / beta * sv[2];
+  if (k == 2) out[2] = -2.0 * sigma2 / (beta * dbeta_div) * sv[2];
   if (k == 3) out[3] = sv[3];
 }
 
@@ -238,7 +242,7 @@ int launch_with(Plan* p, const double* y_dev, const double* theta, bool grad, co
     p->partial_cap = nw * 4;
   }
   const double* tab = nullptr;
-  int rc = get_matern_table(theta[2], stream, &tab);
+  int rc = get_cov_table(p->family, theta[2], stream, &tab);
   if (rc) return rc;
   VECCHIA_CUDA_TRY(cudaMemsetAsync(p->d_errloc, 0xFF, sizeof(unsigned long long), stream));
   LikArgs a;
@@ -249,8 +253,10 @@ int launch_with(Plan* p, const double* y_dev, const double* theta, bool grad, co
   a.tab = tab;
   a.n = p->n;
   a.m = p->m;
+  a.family = p->family;
   a.sigma2 = theta[0];
   a.beta = theta[1];
+  a.nu = theta[2];
   a.tau2 = theta[3];
   a.partial = p->d_partial;
   a.terms = terms_dev;
@@ -258,8 +264,9 @@ int launch_with(Plan* p, const double* y_dev, const double* theta, bool grad, co
   launch_lik(cfg, grad, a, stream);
   VECCHIA_CUDA_TRY(cudaGetLastError());
   if (out_dev) {
-    vecchia_finalize_kernel<<<1, 32, 0, stream>>>(p->d_partial, nw, theta[0], theta[1], theta[3], grad ? 1 : 0,
-                                                  out_dev);
+    const double dbeta_div = p->family == kFamilyPowExp ? theta[2] : 1.0;
+    vecchia_finalize_kernel<<<1, 32, 0, stream>>>(p->d_partial, nw, theta[0], theta[1], theta[3], dbeta_div,
+                                                  grad ? 1 : 0, out_dev);
     VECCHIA_CUDA_TRY(cudaGetLastError());
   }
   p->last_stream = stream;
@@ -269,7 +276,7 @@ int launch_with(Plan* p, const double* y_dev, const double* theta, bool grad, co
 
 int launch_loglik(Plan* p, const double* y_dev, const double* theta, bool grad, double* out_dev,
                   double* terms_dev, cudaStream_t stream) {
-  if (!p || !y_dev || !theta_ok(theta) || (!out_dev && !terms_dev)) return VECCHIA_EINVAL;
+  if (!p || !y_dev || !theta_ok_family(theta, p->family) || (!out_dev && !terms_dev)) return VECCHIA_EINVAL;
   LaunchCfg cfg;
   int rc = pick_config(p->m + 1, grad, &cfg);
   if (rc) return rc;
@@ -280,7 +287,7 @@ int launch_loglik(Plan* p, const double* y_dev, const double* theta, bool grad, 
 // records the fastest for this block size and kind of evaluation.
 int autotune(Plan* p, const double* y_dev, const double* theta, bool grad, int* G_out, int* W_out,
              cudaStream_t stream) {
-  if (!p || !y_dev || !theta_ok(theta)) return VECCHIA_EINVAL;
+  if (!p || !y_dev || !theta_ok_family(theta, p->family)) return VECCHIA_EINVAL;
   const int K = p->m + 1;
   int dev = 0;
   VECCHIA_CUDA_TRY(cudaGetDevice(&dev));
@@ -394,15 +401,17 @@ extern "C" int vecchia_loglik_noalloc(const double* xy_dev, const double* y_dev,
   a.tab = tab;
   a.n = n;
   a.m = m;
+  a.family = kFamilyMatern;
   a.sigma2 = theta[0];
   a.beta = theta[1];
+  a.nu = theta[2];
   a.tau2 = theta[3];
   a.partial = partial;
   a.terms = nullptr;
   a.errloc = errloc;
   launch_lik(cfg, false, a, s);
   VECCHIA_CUDA_TRY(cudaGetLastError());
-  vecchia_finalize_kernel<<<1, 32, 0, s>>>(partial, nw, theta[0], theta[1], theta[3], 0, out_dev);
+  vecchia_finalize_kernel<<<1, 32, 0, s>>>(partial, nw, theta[0], theta[1], theta[3], 1.0, 0, out_dev);
   VECCHIA_CUDA_TRY(cudaGetLastError());
   return VECCHIA_OK;
 }

@@ -42,10 +42,19 @@ __device__ double quad_I(double u, double nu) {
   return acc.value() * h * exp(lpeak);
 }
 
-// One thread: I(0) and the small-u expansion constants.
-__global__ void matern_const_kernel(double nu, double* tab) {
+// One thread: I(0) and the small-u expansion constants (family Matérn), or the
+// exponent (power exponential).
+__global__ void matern_const_kernel(double nu, int family, double* tab) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   double* c = tab + kNInt * kNDbl;
+  if (family == kFamilyPowExp) {
+    c[0] = __longlong_as_double(3LL);
+    c[1] = nu;
+    c[2] = c[3] = c[4] = c[5] = 0.0;
+    c[6] = 1.0;
+    c[7] = 0.0;
+    return;
+  }
   const bool integer = (nu == floor(nu));
   long long kind = integer ? (nu == 1.0 ? 1 : 2) : 0;
   c[0] = __longlong_as_double(kind);
@@ -63,8 +72,9 @@ __global__ void matern_const_kernel(double nu, double* tab) {
   c[7] = 0.0;
 }
 
-// One block of 32 threads per interval.
-__global__ void matern_fit_kernel(double nu, double* tab) {
+// One block of 32 threads per interval.  Node values: the Matérn quadrature, or the
+// power exponential exp(-u^(alpha/2)) (u = (d / beta^(1/alpha))^2) evaluated directly.
+__global__ void matern_fit_kernel(double nu, int family, double* tab) {
   constexpr int N = kDeg + 1;
   __shared__ double f[N], cheb[N], mono[N], tm[N][N];
   const int idx = blockIdx.x;
@@ -77,7 +87,8 @@ __global__ void matern_fit_kernel(double nu, double* tab) {
   const double hw = scale / (2.0 * (1 << kSub));
   if (tid < N) {
     const double tn = cospi((tid + 0.5) / N);
-    f[tid] = quad_I(mid + hw * tn, nu) / I0;
+    const double u = mid + hw * tn;
+    f[tid] = family == kFamilyPowExp ? exp(-exp(0.5 * nu * log(u))) : quad_I(u, nu) / I0;
   }
   if (tid == 0) {
     // Monomial coefficients of T_0..T_kDeg (exact small integers).
@@ -118,6 +129,7 @@ __global__ void matern_fit_kernel(double nu, double* tab) {
 namespace {
 struct TableEntry {
   int device = -1;
+  int family = 0;
   double nu = 0.0;
   double* d_tab = nullptr;
   cudaEvent_t ready = nullptr;
@@ -129,13 +141,14 @@ unsigned long long g_clock = 0;
 constexpr size_t kMaxTables = 16;
 }  // namespace
 
-// Returns (building on `stream` if needed) the device table for nu on the current device.
-int get_matern_table(double nu, cudaStream_t stream, const double** out) {
+// Returns (building on `stream` if needed) the device table for (family, nu) on the
+// current device.
+int get_cov_table(int family, double nu, cudaStream_t stream, const double** out) {
   int dev = 0;
   VECCHIA_CUDA_TRY(cudaGetDevice(&dev));
   std::lock_guard<std::mutex> lk(g_mu);
   for (auto& t : g_tables) {
-    if (t.device == dev && t.nu == nu) {
+    if (t.device == dev && t.family == family && t.nu == nu) {
       VECCHIA_CUDA_TRY(cudaStreamWaitEvent(stream, t.ready, 0));
       t.last_use = ++g_clock;
       *out = t.d_tab;
@@ -162,11 +175,12 @@ int get_matern_table(double nu, cudaStream_t stream, const double** out) {
     cudaEventDestroy(slot->ready);
     *slot = TableEntry();
   }
-  matern_const_kernel<<<1, 32, 0, stream>>>(nu, d);
-  matern_fit_kernel<<<kNInt, 32, 0, stream>>>(nu, d);
+  matern_const_kernel<<<1, 32, 0, stream>>>(nu, family, d);
+  matern_fit_kernel<<<kNInt, 32, 0, stream>>>(nu, family, d);
   VECCHIA_CUDA_TRY(cudaGetLastError());
   VECCHIA_CUDA_TRY(cudaEventRecord(ev, stream));
   slot->device = dev;
+  slot->family = family;
   slot->nu = nu;
   slot->d_tab = d;
   slot->ready = ev;
@@ -175,29 +189,37 @@ int get_matern_table(double nu, cudaStream_t stream, const double** out) {
   return VECCHIA_OK;
 }
 
-// Builds the table for nu into caller-provided device memory (kTableBytes, 16-byte
-// aligned) on `stream`, without touching the cache.
+int get_matern_table(double nu, cudaStream_t stream, const double** out) {
+  return get_cov_table(kFamilyMatern, nu, stream, out);
+}
+
+// Builds the Matérn table for nu into caller-provided device memory (kTableBytes,
+// 16-byte aligned) on `stream`, without touching the cache.
 int launch_matern_table(double nu, double* tab, cudaStream_t stream) {
-  matern_const_kernel<<<1, 32, 0, stream>>>(nu, tab);
-  matern_fit_kernel<<<kNInt, 32, 0, stream>>>(nu, tab);
+  matern_const_kernel<<<1, 32, 0, stream>>>(nu, kFamilyMatern, tab);
+  matern_fit_kernel<<<kNInt, 32, 0, stream>>>(nu, kFamilyMatern, tab);
   VECCHIA_CUDA_TRY(cudaGetLastError());
   return VECCHIA_OK;
 }
 
 // ------------------------------------------------------------------ vecchia_matern
+// C(d) and dC/dbeta through the kernels' device code.  u = (d * inv_len)^2 with the
+// family's length scale (beta for the Matérn, beta^(1/alpha) for the power
+// exponential), and dC/dbeta = dcoef h(u), dcoef = -2 sigma2 / (beta a), a = 1 or alpha.
 __global__ void matern_eval_kernel(const double* __restrict__ d, int64_t count, double sigma2,
-                                   double beta, const double* __restrict__ tab, double* __restrict__ c,
-                                   double* __restrict__ dc) {
+                                   double beta, int family, const double* __restrict__ tab,
+                                   double* __restrict__ c, double* __restrict__ dc) {
   const MaternConst mc = load_matern_const(tab);
-  const double ib = 1.0 / beta;
+  const double inv_len = family == kFamilyPowExp ? exp(-log(beta) / mc.nu) : 1.0 / beta;
+  const double dcoef = -2.0 * sigma2 / (beta * (family == kFamilyPowExp ? mc.nu : 1.0));
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const double x = d[i] * ib;
+    const double x = d[i] * inv_len;
     const double u = x * x;
     double rho, h;
     rho_eval<true>(u, tab, mc, rho, h);
     c[i] = sigma2 * rho;
-    if (dc) dc[i] = -2.0 * sigma2 * ib * h;
+    if (dc) dc[i] = dcoef * h;
   }
 }
 
@@ -208,19 +230,35 @@ bool theta_ok(const double* th) {
   return th[0] > 0.0 && th[1] > 0.0 && th[2] > 0.0 && th[3] >= 0.0;
 }
 
+// theta valid for the family: the power exponential needs 0 < alpha <= 2.
+bool theta_ok_family(const double* th, int family) {
+  return theta_ok(th) && (family != kFamilyPowExp || th[2] <= 2.0);
+}
+
+static int covariance(int family, const double* d_dev, int64_t count, const double* theta, double* c_dev,
+                      double* dcdbeta_dev, cudaStream_t s) {
+  if (count < 0 || (count > 0 && (!d_dev || !c_dev)) || !theta_ok_family(theta, family)) return VECCHIA_EINVAL;
+  if (count == 0) return VECCHIA_OK;
+  const double* tab = nullptr;
+  int rc = get_cov_table(family, theta[2], s, &tab);
+  if (rc) return rc;
+  const int64_t blocks = std::min<int64_t>((count + 255) / 256, 4096);
+  matern_eval_kernel<<<(int)blocks, 256, 0, s>>>(d_dev, count, theta[0], theta[1], family, tab, c_dev,
+                                                 dcdbeta_dev);
+  VECCHIA_CUDA_TRY(cudaGetLastError());
+  return VECCHIA_OK;
+}
+
 }  // namespace vecchia
 
 extern "C" int vecchia_matern(const double* d_dev, int64_t count, const double theta[4], double* c_dev,
                               double* dcdbeta_dev, void* stream) {
-  using namespace vecchia;
-  if (count < 0 || (count > 0 && (!d_dev || !c_dev)) || !theta_ok(theta)) return VECCHIA_EINVAL;
-  if (count == 0) return VECCHIA_OK;
-  cudaStream_t s = (cudaStream_t)stream;
-  const double* tab = nullptr;
-  int rc = get_matern_table(theta[2], s, &tab);
-  if (rc) return rc;
-  const int64_t blocks = std::min<int64_t>((count + 255) / 256, 4096);
-  matern_eval_kernel<<<(int)blocks, 256, 0, s>>>(d_dev, count, theta[0], theta[1], tab, c_dev, dcdbeta_dev);
-  VECCHIA_CUDA_TRY(cudaGetLastError());
-  return VECCHIA_OK;
+  return vecchia::covariance(vecchia::kFamilyMatern, d_dev, count, theta, c_dev, dcdbeta_dev,
+                             (cudaStream_t)stream);
+}
+
+extern "C" int vecchia_covariance(int kernel, const double* d_dev, int64_t count, const double theta[4],
+                                  double* c_dev, double* dcdbeta_dev, void* stream) {
+  if (kernel != VECCHIA_KERNEL_MATERN && kernel != VECCHIA_KERNEL_POWEXP) return VECCHIA_EINVAL;
+  return vecchia::covariance(kernel, d_dev, count, theta, c_dev, dcdbeta_dev, (cudaStream_t)stream);
 }

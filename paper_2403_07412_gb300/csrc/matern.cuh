@@ -25,7 +25,8 @@
 namespace vecchia {
 
 struct MaternConst {
-  // kind: 0 = non-integer nu, 1 = nu == 1, 2 = integer nu >= 2.
+  // kind: Matérn 0 = non-integer nu, 1 = nu == 1, 2 = integer nu >= 2;
+  //       3 = power exponential (nu holds the exponent alpha).
   int kind;
   double nu, a1, G, b0, b1;
 };
@@ -90,7 +91,17 @@ __device__ __forceinline__ double u_dtdu(long long b) {
 //   nu = 1:          rho = 1 + (u/4)(log(u/4) + 2 gamma_E - 1)
 //   integer nu >= 2: rho = 1 - u/(4(nu-1))
 // Omitted terms are O(u^2 log u) or O(u^(nu+2)), below 1e-17 for u < 2^-30.
+// Power exponential, Eq. (3), evaluated directly: with u = (d / beta^(1/alpha))^2,
+// rho = exp(-u^(alpha/2)) and h = u rho' = -(alpha/2) u^(alpha/2) rho.
+static __device__ __noinline__ void rho_powexp(double u, double alpha, double& rho, double& h) {
+  if (u == 0.0) { rho = 1.0; h = 0.0; return; }
+  const double w = exp(0.5 * alpha * log(u));
+  rho = exp(-w);
+  h = -0.5 * alpha * w * rho;
+}
+
 static __device__ __noinline__ void rho_small(double u, const MaternConst& mc, double& rho, double& h) {
+  if (mc.kind == 3) { rho_powexp(u, mc.nu, rho, h); return; }
   if (u == 0.0) { rho = 1.0; h = 0.0; return; }
   const double q = 0.25 * u;
   if (mc.kind == 1) {
@@ -167,22 +178,28 @@ __device__ __forceinline__ double h_poly(double u, const double* __restrict__ ta
   return u_dtdu(b) * dp;
 }
 
-__device__ __forceinline__ double h_fix(double u, const MaternConst& mc, double h) {
-  const int ex = (int)(__double_as_longlong(u) >> 52) - 1023;
-  if (ex >= kEHi) return 0.0;
-  if (ex < kELo) {
-    double r;
-    rho_small(u, mc, r, h);
-  }
-  return h;
-}
 
-// Replaces rho_poly's value outside the tabulated range (rare): far field -> 0,
-// u < 2^kELo -> expansion at zero.
+// Replaces rho_poly's value outside the tabulated range (rare): u < 2^kELo -> the
+// expansion at zero (Matérn) or direct evaluation (power exponential); u >= 2^kEHi ->
+// 0 for the Matérn (below the smallest double), direct evaluation for the power
+// exponential (whose far field decays slowly for small exponents).
 __device__ __forceinline__ void rho_fix(double u, const MaternConst& mc, double& rho, double& h) {
   const int ex = (int)(__double_as_longlong(u) >> 52) - 1023;
-  if (ex >= kEHi) { rho = 0.0; h = 0.0; }
-  else if (ex < kELo) rho_small(u, mc, rho, h);
+  if (ex >= kEHi) {
+    if (mc.kind == 3) rho_powexp(u, mc.nu, rho, h);
+    else { rho = 0.0; h = 0.0; }
+  } else if (ex < kELo) {
+    rho_small(u, mc, rho, h);
+  }
+}
+
+__device__ __forceinline__ double h_fix(double u, const MaternConst& mc, double h) {
+  const int ex = (int)(__double_as_longlong(u) >> 52) - 1023;
+  if (ex >= kEHi || ex < kELo) {
+    double r = 0.0;
+    rho_fix(u, mc, r, h);
+  }
+  return h;
 }
 
 template <bool DERIV>

@@ -490,6 +490,12 @@ void vecchia_plan_destroy(vecchia_plan_t plan) {
   vecchia::plan_free(plan);
 }
 
+int vecchia_plan_set_kernel(vecchia_plan_t plan, int kernel) {
+  if (!plan || (kernel != VECCHIA_KERNEL_MATERN && kernel != VECCHIA_KERNEL_POWEXP)) return VECCHIA_EINVAL;
+  plan->family = kernel;
+  return VECCHIA_OK;
+}
+
 int vecchia_plan_size(vecchia_plan_t plan, int64_t* n, int32_t* m) {
   if (!plan) return VECCHIA_EINVAL;
   if (n) *n = plan->n;

@@ -25,6 +25,7 @@ LIB_PATH = os.path.join(HERE, "libvecchia.so")
 
 OK, EINVAL, ENOTPD, ECUDA, ETIMEOUT, ENOMEM = range(6)
 ORDER_GIVEN, ORDER_RANDOM, ORDER_MAXMIN, ORDER_MORTON = 0, 1, 2, 3
+KERNEL_MATERN, KERNEL_POWEXP = 0, 1
 MAX_M = 63
 
 _lock = threading.Lock()
@@ -41,6 +42,8 @@ SIGNATURES = {
                                            ctypes.POINTER(_i64), _vp, ctypes.POINTER(_vp)]),
     "vecchia_plan_destroy": (None, [_vp]),
     "vecchia_plan_size": (ctypes.c_int, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i32)]),
+    "vecchia_plan_set_kernel": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "vecchia_covariance": (ctypes.c_int, [ctypes.c_int, _vp, _i64, _dp, _vp, _vp, _vp]),
     "vecchia_plan_perm": (ctypes.c_int, [_vp, ctypes.POINTER(_i64)]),
     "vecchia_plan_neighbors": (ctypes.c_int, [_vp, ctypes.POINTER(_i32)]),
     "vecchia_loglik": (ctypes.c_int, [_vp, _vp, _dp, _vp, _vp]),
@@ -141,6 +144,10 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+    def set_kernel(self, kernel: int) -> None:
+        """Covariance family of this plan's likelihood calls (KERNEL_MATERN or KERNEL_POWEXP)."""
+        _check(lib().vecchia_plan_set_kernel(self._h, int(kernel)), "vecchia_plan_set_kernel")
 
     def perm(self) -> np.ndarray:
         out = np.empty(self.n, dtype=np.int64)
@@ -261,6 +268,17 @@ class Batch:
                                           1 if self.want_grad else 0, _vp(out.data_ptr()), _vp(_stream(stream)))
         _check(rc, "vecchia_loglik_batched")
         return out
+
+
+def vecchia_covariance(kernel: int, d: torch.Tensor, theta, with_dbeta: bool = True, stream=None):
+    """C(d) (and dC/dbeta) of either covariance family through the kernels' device code."""
+    d = _dev_f64(d, d.numel(), "d")
+    c = torch.empty_like(d)
+    dc = torch.empty_like(d) if with_dbeta else None
+    rc = lib().vecchia_covariance(int(kernel), _vp(d.data_ptr()), d.numel(), _theta(theta), _vp(c.data_ptr()),
+                                  _vp(dc.data_ptr()) if dc is not None else None, _vp(_stream(stream)))
+    _check(rc, "vecchia_covariance")
+    return (c, dc) if with_dbeta else c
 
 
 def vecchia_fp64_peak(stream=None) -> float:

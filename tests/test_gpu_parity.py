@@ -358,3 +358,40 @@ def test_autotune_records_a_shape(V):
     assert abs(after[0] - before[0]) <= W.LOGLIK_RTOL * den[0]
     for k in (1, 2, 3):
         assert abs(after[k] - before[k]) <= W.GRAD_RTOL * den[k]
+
+
+@pytest.mark.parametrize("alpha", [0.5, 1.0, 1.5, 2.0])
+def test_powexp_covariance_matches_oracle(V, alpha):
+    rng = np.random.default_rng(5)
+    beta, sigma2 = 0.07, 1.1
+    d = np.concatenate([[0.0, 1e-12, 1e-7], np.exp(rng.uniform(-16, 2.5, 20000))])
+    c, dc = V.vecchia_covariance(V.KERNEL_POWEXP, _dev(d), (sigma2, beta, alpha, 0.0))
+    c, dc = c.cpu().numpy(), dc.cpu().numpy()
+    want = oracle.powexp(d, sigma2, beta, alpha)
+    wantd = oracle.powexp_dbeta(d, sigma2, beta, alpha)
+    err = np.abs(c - want)
+    assert np.all(err <= 4e-15 * sigma2), (err.max(), d[np.argmax(err)])
+    ratio = np.abs(dc - wantd) / (2e-9 * np.abs(wantd) + 1e-10 * np.abs(wantd).max())
+    k = int(np.argmax(ratio))
+    assert ratio[k] <= 1.0, (ratio[k], d[k], dc[k], wantd[k])
+    with pytest.raises(V.VecchiaError):
+        V.vecchia_covariance(V.KERNEL_POWEXP, _dev(d[:5]), (sigma2, beta, 2.5, 0.0))
+
+
+@pytest.mark.parametrize("alpha", [0.7, 1.0, 1.9])
+def test_powexp_likelihood_terms_match_oracle(V, alpha):
+    n, m = 3000, 25
+    theta = (1.2, 0.03 ** alpha, alpha, 0.02)
+    xy = datagen.gmm_locations(n, 92)
+    y = datagen.field_rff(xy, (1.0, 0.03, 0.5, 0.02), 93, features=512)
+    perm = oracle.order_random(n, 94)
+    p = _plan_given(V, xy, m, perm)
+    p.set_kernel(V.KERNEL_POWEXP)
+    yd = _dev(y)
+    want = oracle.vecchia_rows(xy[perm], y[perm], m, theta, want_grad=True, family=1)
+    _check_terms(V.vecchia_loglik_terms(p, yd, theta, want_grad=True).cpu().numpy(), want, grad=True)
+    tot = V.vecchia_loglik_grad(p, yd, theta).cpu().numpy()
+    ref = oracle.compensated_sum(want)
+    assert abs(tot[0] - ref[0]) <= W.LOGLIK_RTOL * np.abs(want[:, 0]).sum()
+    for k in (1, 2, 3):
+        assert abs(tot[k] - ref[k]) <= W.GRAD_RTOL * np.abs(want[:, k]).sum(), (k, tot[k], ref[k])

@@ -74,6 +74,33 @@ def test_matern_dbeta_finite_difference(oracle_mod):
     assert oracle_mod.matern_dbeta([0.0], 1.0, 0.1, 1.0)[0] == 0.0
 
 
+def test_powexp_closed_form_and_matern_identity(oracle_mod):
+    # Eq. (3) with exponent 1 is Eq. (2) with nu = 1/2 (both sigma2 exp(-d/beta)).
+    d = np.geomspace(1e-6, 3.0, 300)
+    np.testing.assert_allclose(oracle_mod.powexp(d, 1.4, 0.08, 1.0), oracle_mod.matern(d, 1.4, 0.08, 0.5),
+                               rtol=2e-14)
+    for a in (0.5, 1.5, 2.0):
+        np.testing.assert_allclose(oracle_mod.powexp(d, 0.9, 0.2, a), 0.9 * np.exp(-d ** a / 0.2), rtol=1e-13)
+        h = 1e-6 * 0.2
+        fd = (oracle_mod.powexp(d, 0.9, 0.2 + h, a) - oracle_mod.powexp(d, 0.9, 0.2 - h, a)) / (2 * h)
+        np.testing.assert_allclose(oracle_mod.powexp_dbeta(d, 0.9, 0.2, a), fd, rtol=1e-6, atol=1e-9)
+
+
+def test_powexp_exact_and_vecchia_full_conditioning(oracle_mod):
+    n = 80
+    theta = (1.3, 0.05, 1.5, 0.02)
+    xy = datagen.uniform_locations(n, 91)
+    dd = np.sqrt(((xy[:, None] - xy[None]) ** 2).sum(-1))
+    S = theta[0] * np.exp(-dd ** theta[2] / theta[1]) + theta[3] * np.eye(n)
+    y = np.linalg.cholesky(S) @ np.random.default_rng(1).standard_normal(n)
+    want = multivariate_normal(mean=np.zeros(n), cov=S).logpdf(y)
+    ex, gex = oracle_mod.loglik_exact(xy, y, theta, want_grad=True, family=1)
+    assert _rel(ex, want) < 1e-10
+    va = oracle_mod.vecchia(xy, y, n - 1, theta, want_grad=True, family=1)
+    assert _rel(va[0], ex) < 1e-10
+    np.testing.assert_allclose(va[1:], gex, rtol=1e-8, atol=1e-8 * np.abs(gex).max())
+
+
 # ----------------------------------------------------------------- orderings
 def test_splitmix64_published_vector(oracle_mod):
     want = [int(l, 16) for l in open(os.path.join(GOLDEN, "splitmix64_seed0.txt")) if l.startswith("0x")]
