@@ -61,8 +61,11 @@ enum {
   VECCHIA_KERNEL_POWEXP = 1  /* Eq. (3): sigma2 exp(-d^nu / beta), 0 < nu <= 2 (nu = the exponent) */
 };
 
-/* Largest conditioning-set size m accepted by the likelihood kernels. */
-#define VECCHIA_MAX_M 63
+/* Largest conditioning-set size m accepted by plans and the single-field likelihood
+ * calls; up to VECCHIA_MAX_M_WARP a warp (or part of one) owns a location, beyond it a
+ * CTA does.  The batched and allocation-free calls accept m <= VECCHIA_MAX_M_WARP. */
+#define VECCHIA_MAX_M 150
+#define VECCHIA_MAX_M_WARP 63
 
 /*
  * vecchia_plan_create — ordering and conditioning sets (Algorithm 1, permutation and
@@ -183,7 +186,7 @@ int vecchia_batched_prepare(const double* nus, int32_t nnu, void* stream);
  * vecchia_loglik_batched — many (field, theta) evaluations in one persistent launch (not
  * in the paper, which batches only over the locations of one field).
  *   plans      : nfields plan handles (host array); fields may differ in n and m (at most
- *                four distinct m per call).
+ *                four distinct m per call, each m <= VECCHIA_MAX_M_WARP).
  *   y_devs     : nfields device pointers (host array), field f's n values in the ORIGINAL
  *                order of plans[f].
  *   thetas_dev : nfields x ntheta x 4 doubles on the DEVICE, row-major; each theta's nu
@@ -222,7 +225,7 @@ int vecchia_loglik_batched(const vecchia_plan_t* plans, const double* const* y_d
  *              ORIGINAL indices, -1 padded after m_i = min(i, m) entries; from a plan:
  *              perm[vecchia_plan_neighbors()] for entries >= 0.
  *   self_dev : n int32, ORIGINAL index of the i-th ordered location (= perm[i]).
- *   n, m     : 1 <= n <= 2^31 - 1, 1 <= m <= VECCHIA_MAX_M; otherwise EINVAL.
+ *   n, m     : 1 <= n <= 2^31 - 1, 1 <= m <= VECCHIA_MAX_M_WARP; otherwise EINVAL.
  *   theta    : host double[4] as for vecchia_loglik; out_dev: 1 double on the device.
  * Asynchronous on `stream`.  The first call on a device looks up the scratch array's
  * device address (cudaGetSymbolAddress); make that first call before any stream

@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libvecchia.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["matern.cu", "loglik.cu", "plan.cu", "peak.cu", "batched.cu"]
+SOURCES = ["matern.cu", "loglik.cu", "plan.cu", "peak.cu", "batched.cu", "bigblock.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -1,0 +1,333 @@
+// Large conditioning sets (m > VECCHIA_MAX_M_WARP): one CTA per location.
+//
+// The paper runs m up to 150 (Sec. VI-D).  A 151-row bordered block is 93 KB of packed
+// FP64, too much for a warp's share of shared memory, so here a CTA of kCtaThreads
+// threads owns one location at a time and runs the same elimination as block.cuh (the
+// bordered L D L^T whose trailing 2x2 corner holds s_i / sigma2 and y_i - mu_i) with
+// CTA-wide barriers.  The (row, column) of a packed slot or a pair index is decoded
+// arithmetically (a triangular-number inverse) instead of from schedule tables, which
+// keeps two CTAs resident per SM.  The adjoint's two backward solves run on the first
+// warp (shuffles); everything else is spread over all threads.
+#include <algorithm>
+#include <cmath>
+
+#include "block.cuh"
+#include "common.cuh"
+#include "matern.cuh"
+
+namespace vecchia {
+
+constexpr int kCtaThreads = 128;
+
+struct BigArgs {
+  const double* __restrict__ xy;
+  const double* __restrict__ yf;
+  const int32_t* __restrict__ nbr;
+  const int32_t* __restrict__ self;
+  const double* __restrict__ tab;
+  int64_t n;
+  int m;
+  int family;
+  double sigma2, beta, nu, tau2;
+  double* partial;  // [gridDim.x][4]
+  double* terms;
+  unsigned long long* errloc;
+};
+
+// Largest w with w(w+1)/2 <= e (e < 2^24).
+__device__ __forceinline__ int tri_root(int e) {
+  int w = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+  if ((w + 1) * (w + 2) / 2 <= e) ++w;
+  if (w * (w + 1) / 2 > e) --w;
+  return w;
+}
+
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += red[k];
+  return s;
+}
+
+template <bool GRAD>
+__global__ void __launch_bounds__(kCtaThreads) vecchia_big_kernel(const BigArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int m = a.m, K = m + 1;
+  const int NTd = (K + 1) * (K + 2) / 2, NP = K * (K - 1) / 2;
+  double* A = reinterpret_cast<double*>(smem);
+  long long* QX = reinterpret_cast<long long*>(A + align_up(NTd, 2));
+  long long* QY = QX + align_up(K + 1, 2);
+  double* YV = reinterpret_cast<double*>(QY + align_up(K + 1, 2));
+  double* TV = YV + align_up(K + 1, 2);
+  double* WH = TV + align_up(K + 1, 2);
+  double* GV = WH + align_up(K + 1, 2);
+  double* red = GV + align_up(K + 1, 2);
+  int* ired = reinterpret_cast<int*>(red + 32);
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int NTH = blockDim.x;
+  const MaternConst mc = load_matern_const(a.tab);
+  ThetaConst tc;
+  tc.set(a.sigma2, a.beta, a.tau2, a.family, a.nu);
+  const double2* __restrict__ xy2 = reinterpret_cast<const double2*>(a.xy);
+  Accum acc;
+  for (int64_t i = blockIdx.x; i < a.n; i += gridDim.x) {
+    const int mi = i < m ? (int)i : m;
+    const int32_t* __restrict__ row = a.nbr + i * m;
+    const int js = a.self[i];
+    const double2 ps = xy2[js];
+    // ---- gather (two slots per thread covers m <= 2 * kCtaThreads)
+    double xv[2] = {0.0, 0.0}, yv[2] = {0.0, 0.0};
+    int emax = 0;
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      const int p = tid + NTH * s;
+      if (p < m) {
+        double fv = 0.0;
+        if (p < mi) {
+          const int j = row[p];
+          const double2 q = xy2[j];
+          xv[s] = (q.x - ps.x) * tc.inv_len;
+          yv[s] = (q.y - ps.y) * tc.inv_len;
+          fv = a.yf[j];
+        }
+        YV[p] = fv;
+        emax = max(emax, (int)((__double_as_longlong(xv[s]) >> 52) & 0x7FF));
+        emax = max(emax, (int)((__double_as_longlong(yv[s]) >> 52) & 0x7FF));
+      }
+    }
+    emax = __reduce_max_sync(0xffffffffu, emax);
+    if (lane == 0) ired[wid] = emax;
+    __syncthreads();
+    for (int k = 0; k < NTH / 32; ++k) emax = max(emax, ired[k]);
+    const int FX = emax == 0 ? 0 : 61 - (emax - 1023);
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      const int p = tid + NTH * s;
+      if (p < m) {
+        QX[p] = to_fixed(xv[s], FX);
+        QY[p] = to_fixed(yv[s], FX);
+      }
+    }
+    if (tid == 0) {
+      QX[m] = 0;
+      QY[m] = 0;
+      YV[m] = a.yf[js];
+    }
+    __syncthreads();
+    // ---- assemble
+    for (int c = tid; c < K; c += NTH) {
+      const int o = tri_off(K, c);
+      A[o] = (c >= mi && c < m) ? 1.0 : tc.gamma1;
+      A[o + K - c] = YV[c];
+    }
+    if (tid == 0) A[0] = 0.0;
+    for (int q0 = tid; q0 < NP; q0 += 2 * NTH) {
+      const int q1 = q0 + NTH;
+      const bool has1 = q1 < NP;
+      const int v0 = tri_root(q0), v1 = tri_root(has1 ? q1 : q0);
+      const int c0 = K - 2 - v0, r0 = c0 + 1 + (q0 - v0 * (v0 + 1) / 2);
+      const int qq1 = has1 ? q1 : q0;
+      const int c1 = K - 2 - v1, r1 = c1 + 1 + (qq1 - v1 * (v1 + 1) / 2);
+      const bool ok0 = c0 < mi && (r0 < mi || r0 == m);
+      const bool ok1 = has1 && c1 < mi && (r1 < mi || r1 == m);
+      const double u0 = fixed_sq_dist(QX[r0] - QX[c0], QY[r0] - QY[c0], FX);
+      const double u1 = fixed_sq_dist(QX[r1] - QX[c1], QY[r1] - QY[c1], FX);
+      double val0, hv0, val1, hv1;
+      rho_poly<false>(u0, a.tab, val0, hv0);
+      rho_poly<false>(u1, a.tab, val1, hv1);
+      rho_fix(u0, mc, val0, hv0);
+      rho_fix(u1, mc, val1, hv1);
+      A[tri_off(K, c0) + r0 - c0] = ok0 ? val0 : 0.0;
+      if (has1) A[tri_off(K, c1) + r1 - c1] = ok1 ? val1 : 0.0;
+    }
+    __syncthreads();
+    // ---- L D L^T over the neighbour columns (CTA-wide steps)
+    bool ok = true;
+    for (int j = 0; j < K - 1; ++j) {
+      const int oj = tri_off(K, j);
+      const double d = A[oj];
+      if (!positive_finite(d)) { ok = false; break; }  // uniform over the CTA
+      const double inv = rcp_newton(d);
+      for (int r = j + 1 + tid; r <= K; r += NTH) {
+        const double tv = A[oj + r - j];
+        TV[r] = tv;
+        A[oj + r - j] = tv * inv;
+      }
+      __syncthreads();
+      const double* Lc = A + oj - j;
+      constexpr int U = 8;
+      const int nfull = (oj - 1) / (NTH * U);
+      const int tail0 = 1 + NTH * U * nfull;
+      for (int bt = 0; bt < nfull; ++bt) {
+        const int base = 1 + tid + NTH * U * bt;
+        double lv[U], tv[U], av[U];
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+          const int e = base + NTH * k;
+          const int w = tri_root(e);
+          const int c = K - w, r = c + (e - w * (w + 1) / 2);
+          lv[k] = Lc[r];
+          tv[k] = TV[c];
+          av[k] = A[e];
+        }
+#pragma unroll
+        for (int k = 0; k < U; ++k) A[base + NTH * k] = fma(-lv[k], tv[k], av[k]);
+      }
+      for (int e = tail0 + tid; e < oj; e += NTH) {
+        const int w = tri_root(e);
+        const int c = K - w, r = c + (e - w * (w + 1) / 2);
+        A[e] = fma(-Lc[r], TV[c], A[e]);
+      }
+      __syncthreads();
+    }
+    const double st = A[1], rr = A[2];
+    const bool good = ok && positive_finite(st);
+    const double nan = __longlong_as_double(0x7FF8000000000000LL);
+    const double s = tc.sigma2 * st;
+    const double inv_s = rcp_newton(s);
+    const double q = rr * rr * inv_s;
+    if (good) {
+      acc.Q.add(q);
+      acc.mul_s(s);
+      acc.count += 1;
+    } else {
+      acc.Q.add(nan);
+      if (tid == 0) atomicMin(a.errloc, (unsigned long long)i);
+    }
+    const double li = good ? -0.5 * q - 0.5 * log(s) - 0.91893853320467274178 : nan;
+    if (!GRAD) {
+      if (a.terms && tid == 0) a.terms[i] = li;
+      __syncthreads();
+      continue;
+    }
+    // ---- adjoint: backward solves on warp 0, then the pair pass on all threads
+    const double rs = rr * inv_s;
+    const double cb = 0.5 * (rs * rs - inv_s);
+    const double rsa = rs * tc.inv_sigma2;
+    double pT = 0.0;
+    if (wid == 0 && good) {
+      constexpr int NS = (kMaxM + 31) / 32;
+      double w[NS], bv[NS];
+#pragma unroll
+      for (int t = 0; t < NS; ++t) {
+        const int c = lane + 32 * t;
+        w[t] = 0.0;
+        bv[t] = 0.0;
+        if (c < K - 1) {
+          const int o = tri_off(K, c);
+          w[t] = A[o + m - c];
+          bv[t] = A[o + K - c];
+        }
+      }
+      for (int c = K - 2; c >= 1; --c) {
+        const int src = c & 31, sl = c >> 5;
+        double wsel = w[0], bsel = bv[0];
+#pragma unroll
+        for (int t = 1; t < NS; ++t)
+          if (sl == t) {
+            wsel = w[t];
+            bsel = bv[t];
+          }
+        const double wc = __shfl_sync(0xffffffffu, wsel, src);
+        const double bc = __shfl_sync(0xffffffffu, bsel, src);
+#pragma unroll
+        for (int t = 0; t < NS; ++t) {
+          const int cc = lane + 32 * t;
+          if (cc < c) {
+            const double l = A[tri_off(K, cc) + c - cc];
+            w[t] = fma(-l, wc, w[t]);
+            bv[t] = fma(-l, bc, bv[t]);
+          }
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < NS; ++t) {
+        const int c = lane + 32 * t;
+        if (c < K - 1) {
+          const double wh = -w[t], gv = fma(rsa, bv[t], cb * wh);
+          WH[c] = wh;
+          GV[c] = gv;
+          pT = fma(wh, gv, pT);
+        }
+      }
+      if (lane == 0) {
+        WH[m] = 1.0;
+        GV[m] = cb;
+        pT += cb;
+      }
+    }
+    __syncthreads();
+    double pB = 0.0;
+    if (good) {
+      for (int q0 = tid; q0 < NP; q0 += NTH) {
+        const int v0 = tri_root(q0);
+        const int c0 = K - 2 - v0, r0 = c0 + 1 + (q0 - v0 * (v0 + 1) / 2);
+        const double u0 = fixed_sq_dist(QX[r0] - QX[c0], QY[r0] - QY[c0], FX);
+        const double h0 = h_fix(u0, mc, h_poly(u0, a.tab));
+        double t0 = WH[r0] * GV[c0];
+        t0 = fma(WH[c0], GV[r0], t0);
+        pB = fma(h0, t0, pB);
+      }
+    }
+    const double sS = 0.5 * (rr * rs - 1.0);
+    if (a.terms) {
+      const double tB = block_sum(pB, red), tT = block_sum(pT, red);
+      if (tid == 0) {
+        double* o = a.terms + i * 4;
+        o[0] = li;
+        o[1] = good ? (sS - tc.tau2 * tT) * tc.inv_sigma2 : nan;
+        o[2] = good ? tc.dbeta_coef * tB : nan;
+        o[3] = good ? tT : nan;
+      }
+    }
+    if (good) {
+      acc.S += sS;
+      acc.B += pB;
+      acc.T += pT;
+    } else {
+      acc.S += nan;
+    }
+    __syncthreads();
+  }
+  const double B = block_sum(acc.B, red);
+  const double T = block_sum(acc.T, red);
+  if (tid == 0) {
+    double* o = a.partial + (int64_t)blockIdx.x * 4;
+    o[0] = acc.loglik();
+    o[1] = acc.S;
+    o[2] = B;
+    o[3] = T;
+  }
+}
+
+// Shared memory of the CTA kernel for block size K.
+int big_smem_bytes(int K) {
+  const int NTd = (K + 1) * (K + 2) / 2;
+  return 8 * (align_up(NTd, 2) + 6 * align_up(K + 1, 2) + 32 + 16);
+}
+
+// Persistent grid: resident CTAs per SM x SMs.
+int big_config(int K, bool grad, int* blocks, int* smem) {
+  int dev = 0, sms = 0;
+  VECCHIA_CUDA_TRY(cudaGetDevice(&dev));
+  VECCHIA_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  *smem = big_smem_bytes(K);
+  auto kern = grad ? vecchia_big_kernel<true> : vecchia_big_kernel<false>;
+  VECCHIA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, *smem));
+  int per_sm = 0;
+  VECCHIA_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kCtaThreads, *smem));
+  if (per_sm < 1) return VECCHIA_EINVAL;
+  *blocks = per_sm * sms;
+  return VECCHIA_OK;
+}
+
+void launch_big(bool grad, int blocks, int smem, const BigArgs& a, cudaStream_t s) {
+  if (grad) vecchia_big_kernel<true><<<blocks, kCtaThreads, smem, s>>>(a);
+  else vecchia_big_kernel<false><<<blocks, kCtaThreads, smem, s>>>(a);
+}
+
+}  // namespace vecchia

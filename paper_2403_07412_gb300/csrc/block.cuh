@@ -219,7 +219,7 @@ __device__ __forceinline__ void process_location(int64_t i, bool active, const F
                                                  const double* __restrict__ tab, const MaternConst& mc,
                                                  const ThetaConst& tc, Accum& acc, bool terms_mode,
                                                  double* terms, unsigned long long* errloc, int sub) {
-  constexpr int NSG = (kMaxM + G) / G;  // neighbour slots per lane (m <= kMaxM)
+  constexpr int NSG = (kMaxMWarp + G) / G;  // neighbour slots per lane (m <= kMaxMWarp)
   const int m = F.m;
   const int K = m + 1;
   double* __restrict__ A = W.A;
@@ -380,7 +380,7 @@ __device__ __forceinline__ void process_location(int64_t i, bool active, const F
   // ---- adjoint: w = L_J^{-T} (row m of L), alpha~ = L_J^{-T} (row K of L)
   double* __restrict__ WH = W.WH;
   double* __restrict__ GV = W.GV;
-  constexpr int NS = (kMaxM + G - 1) / G;  // slots of the K-1 <= kMaxM neighbour entries
+  constexpr int NS = (kMaxMWarp + G - 1) / G;  // slots of the K-1 <= kMaxMWarp neighbour entries
   double w[NS], bv[NS];
 #pragma unroll
   for (int t = 0; t < NS; ++t) {

@@ -27,9 +27,9 @@ constexpr int kNFlt = 12;
 constexpr int kNConst = 8;
 constexpr size_t kTableBytes = sizeof(double) * (kNInt * kNDbl + kNConst) + sizeof(float) * kNInt * kNFlt;
 
-// Largest bordered block: m + 2 rows (m neighbours, the location, the data border).
+// Largest conditioning sets: overall (CTA-per-location kernel) and for the warp kernels.
 constexpr int kMaxM = VECCHIA_MAX_M;
-constexpr int kMaxK = kMaxM + 1;
+constexpr int kMaxMWarp = VECCHIA_MAX_M_WARP;
 
 // Covariance families (VECCHIA_KERNEL_*): Matérn, Eq. (2); power exponential, Eq. (3).
 constexpr int kFamilyMatern = 0;

@@ -19,6 +19,23 @@ namespace vecchia {
 
 int get_matern_table(double nu, cudaStream_t stream, const double** out);
 int get_cov_table(int family, double nu, cudaStream_t stream, const double** out);
+
+struct BigArgs {
+  const double* __restrict__ xy;
+  const double* __restrict__ yf;
+  const int32_t* __restrict__ nbr;
+  const int32_t* __restrict__ self;
+  const double* __restrict__ tab;
+  int64_t n;
+  int m;
+  int family;
+  double sigma2, beta, nu, tau2;
+  double* partial;
+  double* terms;
+  unsigned long long* errloc;
+};
+int big_config(int K, bool grad, int* blocks, int* smem);
+void launch_big(bool grad, int blocks, int smem, const BigArgs& a, cudaStream_t s);
 bool theta_ok_family(const double* th, int family);
 int launch_matern_table(double nu, double* tab, cudaStream_t stream);
 bool theta_ok(const double* th);
@@ -274,9 +291,55 @@ int launch_with(Plan* p, const double* y_dev, const double* theta, bool grad, co
 }
 }  // namespace
 
+// Blocks beyond the warp kernels' size: one CTA per location (bigblock.cu).
+static int launch_big_loglik(Plan* p, const double* y_dev, const double* theta, bool grad, double* out_dev,
+                             double* terms_dev, cudaStream_t stream) {
+  int blocks = 0, smem = 0;
+  int rc = big_config(p->m + 1, grad, &blocks, &smem);
+  if (rc) return rc;
+  if (p->partial_cap < (int64_t)blocks * 4) {
+    if (p->d_partial) cudaFree(p->d_partial);
+    p->d_partial = nullptr;
+    p->partial_cap = 0;
+    if (cudaMalloc(&p->d_partial, sizeof(double) * blocks * 4) != cudaSuccess) return VECCHIA_ENOMEM;
+    p->partial_cap = (int64_t)blocks * 4;
+  }
+  const double* tab = nullptr;
+  rc = get_cov_table(p->family, theta[2], stream, &tab);
+  if (rc) return rc;
+  VECCHIA_CUDA_TRY(cudaMemsetAsync(p->d_errloc, 0xFF, sizeof(unsigned long long), stream));
+  BigArgs a;
+  a.xy = p->d_xy;
+  a.yf = y_dev;
+  a.nbr = p->d_nbr;
+  a.self = p->d_self;
+  a.tab = tab;
+  a.n = p->n;
+  a.m = p->m;
+  a.family = p->family;
+  a.sigma2 = theta[0];
+  a.beta = theta[1];
+  a.nu = theta[2];
+  a.tau2 = theta[3];
+  a.partial = p->d_partial;
+  a.terms = terms_dev;
+  a.errloc = p->d_errloc;
+  launch_big(grad, blocks, smem, a, stream);
+  VECCHIA_CUDA_TRY(cudaGetLastError());
+  if (out_dev) {
+    const double dbeta_div = p->family == kFamilyPowExp ? theta[2] : 1.0;
+    vecchia_finalize_kernel<<<1, 32, 0, stream>>>(p->d_partial, blocks, theta[0], theta[1], theta[3], dbeta_div,
+                                                  grad ? 1 : 0, out_dev);
+    VECCHIA_CUDA_TRY(cudaGetLastError());
+  }
+  p->last_stream = stream;
+  return VECCHIA_OK;
+}
+
 int launch_loglik(Plan* p, const double* y_dev, const double* theta, bool grad, double* out_dev,
                   double* terms_dev, cudaStream_t stream) {
   if (!p || !y_dev || !theta_ok_family(theta, p->family) || (!out_dev && !terms_dev)) return VECCHIA_EINVAL;
+  if (p->m > kMaxMWarp) return launch_big_loglik(p, y_dev, theta, grad, out_dev, terms_dev, stream);
   LaunchCfg cfg;
   int rc = pick_config(p->m + 1, grad, &cfg);
   if (rc) return rc;
@@ -289,6 +352,11 @@ int autotune(Plan* p, const double* y_dev, const double* theta, bool grad, int* 
              cudaStream_t stream) {
   if (!p || !y_dev || !theta_ok_family(theta, p->family)) return VECCHIA_EINVAL;
   const int K = p->m + 1;
+  if (p->m > kMaxMWarp) {  // one CTA of 4 warps per location: nothing to choose
+    if (G_out) *G_out = 128;
+    if (W_out) *W_out = 4;
+    return VECCHIA_OK;
+  }
   int dev = 0;
   VECCHIA_CUDA_TRY(cudaGetDevice(&dev));
   double* out = nullptr;
@@ -373,7 +441,7 @@ extern "C" int vecchia_loglik_noalloc(const double* xy_dev, const double* y_dev,
                                       double* out_dev, void* stream) {
   using namespace vecchia;
   if (!xy_dev || !y_dev || !nbr_dev || !self_dev || !out_dev || n < 1 || n > 2147483647LL || m < 1 ||
-      m > kMaxM || !theta_ok(theta))
+      m > kMaxMWarp || !theta_ok(theta))
     return VECCHIA_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   unsigned char* base = nullptr;

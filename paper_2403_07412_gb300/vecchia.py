@@ -26,7 +26,8 @@ LIB_PATH = os.path.join(HERE, "libvecchia.so")
 OK, EINVAL, ENOTPD, ECUDA, ETIMEOUT, ENOMEM = range(6)
 ORDER_GIVEN, ORDER_RANDOM, ORDER_MAXMIN, ORDER_MORTON = 0, 1, 2, 3
 KERNEL_MATERN, KERNEL_POWEXP = 0, 1
-MAX_M = 63
+MAX_M = 150
+MAX_M_WARP = 63
 
 _lock = threading.Lock()
 _lib = None

@@ -52,7 +52,7 @@ def test_strerror_and_argument_checks_without_gpu(libpath):
     assert L.vecchia_plan_create(None, 10, 5, 1, 0, None, None, ctypes.byref(out)) == vecchia.EINVAL
     xy = (ctypes.c_double * 4)(0.1, 0.2, 0.3, 0.4)
     assert L.vecchia_plan_create(xy, 2, 0, 1, 0, None, None, ctypes.byref(out)) == vecchia.EINVAL
-    assert L.vecchia_plan_create(xy, 2, 64, 1, 0, None, None, ctypes.byref(out)) == vecchia.EINVAL
+    assert L.vecchia_plan_create(xy, 2, 151, 1, 0, None, None, ctypes.byref(out)) == vecchia.EINVAL
     assert L.vecchia_plan_create(xy, 2, 5, 7, 0, None, None, ctypes.byref(out)) == vecchia.EINVAL
     bad = (ctypes.c_double * 4)(0.1, float("nan"), 0.3, 0.4)
     assert L.vecchia_plan_create(bad, 2, 1, 1, 0, None, None, ctypes.byref(out)) == vecchia.EINVAL

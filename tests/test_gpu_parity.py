@@ -395,3 +395,30 @@ def test_powexp_likelihood_terms_match_oracle(V, alpha):
     assert abs(tot[0] - ref[0]) <= W.LOGLIK_RTOL * np.abs(want[:, 0]).sum()
     for k in (1, 2, 3):
         assert abs(tot[k] - ref[k]) <= W.GRAD_RTOL * np.abs(want[:, k]).sum(), (k, tot[k], ref[k])
+
+
+@pytest.mark.parametrize("m", [64, 90, 150])
+def test_large_conditioning_sets_match_oracle(V, m):
+    # m beyond the warp kernels: one CTA per location (the paper runs m up to 150).
+    n = 1200
+    theta = (1.3, 0.08, 1.0, 0.02)
+    xy = datagen.uniform_locations(n, 100 + m)
+    y = datagen.field_rff(xy, theta, 101 + m, features=512)
+    perm = oracle.order_random(n, 102 + m)
+    p = _plan_given(V, xy, m, perm)
+    np.testing.assert_array_equal(p.neighbors(), oracle.knn_rows(xy[perm], m))
+    yd = _dev(y)
+    want = oracle.vecchia_rows(xy[perm], y[perm], m, theta, want_grad=True)
+    _check_terms(V.vecchia_loglik_terms(p, yd, theta, want_grad=True).cpu().numpy(), want, grad=True)
+    _check_terms(V.vecchia_loglik_terms(p, yd, theta).cpu().numpy(), want[:, 0])
+    tot = V.vecchia_loglik_grad(p, yd, theta).cpu().numpy()
+    ref = oracle.compensated_sum(want)
+    assert abs(tot[0] - ref[0]) <= W.LOGLIK_RTOL * np.abs(want[:, 0]).sum()
+    for k in (1, 2, 3):
+        assert abs(tot[k] - ref[k]) <= W.GRAD_RTOL * np.abs(want[:, k]).sum()
+    if m == 150:  # m = n - 1 is exact: the Vecchia product is Eq. (1)
+        xs = xy[:151]
+        ys = y[:151]
+        p2 = V.Plan(xs, 150)
+        got = V.vecchia_loglik(p2, _dev(ys), theta).cpu().numpy()[0]
+        assert abs(got - oracle.loglik_exact(xs, ys, theta)) <= 1e-9 * abs(got)

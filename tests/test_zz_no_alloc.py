@@ -53,4 +53,4 @@ def test_noalloc_matches_plan_entry_point_twice():
     # arguments outside the limits are rejected before any device work
     assert L.vecchia_loglik_noalloc(ctypes.c_void_p(xy_d.data_ptr()), ctypes.c_void_p(y_d.data_ptr()),
                                     ctypes.c_void_p(nbr_d.data_ptr()), ctypes.c_void_p(self_d.data_ptr()),
-                                    n, V.MAX_M + 1, th, ctypes.c_void_p(out.data_ptr()), stream) == V.EINVAL
+                                    n, V.MAX_M_WARP + 1, th, ctypes.c_void_p(out.data_ptr()), stream) == V.EINVAL
