@@ -183,6 +183,41 @@ def run_batched(V, dev, peak_tflops, nfields=64, ntheta=32, scale=1.0, reps=1):
             "result_finite": bool(np.all(np.isfinite(res))), "setup_seconds": round(setup_s, 1)}
 
 
+def run_m_sweep(V, dev, peak_tflops, n=250_000, ms=(10, 30, 60, 90, 120, 150)):
+    """One evaluation per conditioning size, as in the paper's performance study
+    (time and flop rate of a single likelihood evaluation vs m): n uniform locations,
+    random ordering, Matérn nu = 1.5."""
+    import torch
+    from paper_2403_07412_gb300 import datagen
+
+    seed = datagen.BASE_SEED + 6
+    xy = datagen.uniform_locations(n, seed)
+    theta = (1.0, 0.03, 1.5, 0.01)
+    y = torch.as_tensor(datagen.field_rff(xy, theta, seed + 1000, device=dev), device=dev)
+    out = torch.empty(4, dtype=torch.float64, device=dev)
+    rows = []
+    for m in ms:
+        plan = V.Plan(xy, m, order=V.ORDER_RANDOM, seed=seed)
+        row = {"m": m, "n": n}
+        for name, fn, grad in (("fwd", V.vecchia_loglik, False), ("grad", V.vecchia_loglik_grad, True)):
+            fn(plan, y, theta, out=out)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(3):
+                fn(plan, y, theta, out=out)
+            e1.record()
+            torch.cuda.synchronize()
+            ms_call = e0.elapsed_time(e1) / 3
+            tf = la_flops(n, m, grad) / (ms_call * 1e-3) / 1e12
+            row[name] = {"ms": round(ms_call, 3), "locations_per_s": n / (ms_call * 1e-3),
+                         "tflops": round(tf, 4), "frac_of_fp64_peak": round(tf / peak_tflops, 4)}
+        plan.close()
+        rows.append(row)
+    return rows
+
+
 def cpu_baseline(xy, y, theta, m, budget_s):
     """The oracle, as it stands, on a bounded random sample of rows of the same workload
     (its own random ordering and brute-force conditioning sets; neighbour search untimed)."""
@@ -265,6 +300,7 @@ def main():
     ap.add_argument("--ref-budget", type=float, default=90.0, help="seconds for the whole reference run")
     ap.add_argument("--fwd", action="store_true", help="time the forward-only kernel instead")
     ap.add_argument("--no-batched", action="store_true", help="skip the many-field batched measurement")
+    ap.add_argument("--no-m-sweep", action="store_true", help="skip the conditioning-size sweep")
     ap.add_argument("--batched-scale", type=float, default=1.0, help="scale of the batched fields' sizes")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -440,6 +476,8 @@ def main():
                            "frac_of_fp64_peak": ff / (fwd_ms * 1e-3) / 1e12 / peak}
     if not args.no_batched:
         line["batched"] = run_batched(V, dev, peak, scale=args.batched_scale)
+    if not args.no_m_sweep:
+        line["m_sweep"] = run_m_sweep(V, dev, peak)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(xy, y, theta, m, args.cpu_budget)
     print(json.dumps(line), flush=True)

@@ -10,6 +10,7 @@
 // warp (shuffles); everything else is spread over all threads.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 
 #include "block.cuh"
 #include "common.cuh"
@@ -17,7 +18,8 @@
 
 namespace vecchia {
 
-constexpr int kCtaThreads = 128;
+constexpr int kCtaThreads = 128;     // default CTA size (4 warps)
+constexpr int kCtaThreadsMax = 256;  // when fewer than 4 CTAs fit on an SM
 
 struct BigArgs {
   const double* __restrict__ xy;
@@ -54,7 +56,7 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 }
 
 template <bool GRAD>
-__global__ void __launch_bounds__(kCtaThreads) vecchia_big_kernel(const BigArgs a) {
+__global__ void __launch_bounds__(kCtaThreadsMax) vecchia_big_kernel(const BigArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int m = a.m, K = m + 1;
   const int NTd = (K + 1) * (K + 2) / 2, NP = K * (K - 1) / 2;
@@ -310,24 +312,39 @@ int big_smem_bytes(int K) {
   return 8 * (align_up(NTd, 2) + 6 * align_up(K + 1, 2) + 32 + 16);
 }
 
-// Persistent grid: resident CTAs per SM x SMs.
-int big_config(int K, bool grad, int* blocks, int* smem) {
+// CTA size: 128 threads while at least 4 CTAs fit on an SM (more locations in flight),
+// else 256 so that the SM still holds 512 threads.  Measured on GB300 at n = 100k:
+// m = 90 (6 CTAs/SM) 128 threads 1.35x faster than 256; m = 150 (2 CTAs/SM) 256
+// threads 1.34x faster than 128.  VECCHIA_CTA_THREADS = 128 or 256 forces one.
+int big_config(int K, bool grad, int* blocks, int* threads, int* smem) {
   int dev = 0, sms = 0;
   VECCHIA_CUDA_TRY(cudaGetDevice(&dev));
   VECCHIA_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   *smem = big_smem_bytes(K);
   auto kern = grad ? vecchia_big_kernel<true> : vecchia_big_kernel<false>;
   VECCHIA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, *smem));
+  const char* e = getenv("VECCHIA_CTA_THREADS");
+  const int forced = e ? atoi(e) : 0;
+  int t = (forced == 128 || forced == 256) ? forced : kCtaThreads;
   int per_sm = 0;
-  VECCHIA_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kCtaThreads, *smem));
+  VECCHIA_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, t, *smem));
+  if (forced != 128 && forced != 256 && per_sm * t < 512) {
+    int per_sm2 = 0;
+    VECCHIA_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, kern, kCtaThreadsMax, *smem));
+    if (per_sm2 >= 1) {
+      t = kCtaThreadsMax;
+      per_sm = per_sm2;
+    }
+  }
   if (per_sm < 1) return VECCHIA_EINVAL;
   *blocks = per_sm * sms;
+  *threads = t;
   return VECCHIA_OK;
 }
 
-void launch_big(bool grad, int blocks, int smem, const BigArgs& a, cudaStream_t s) {
-  if (grad) vecchia_big_kernel<true><<<blocks, kCtaThreads, smem, s>>>(a);
-  else vecchia_big_kernel<false><<<blocks, kCtaThreads, smem, s>>>(a);
+void launch_big(bool grad, int blocks, int threads, int smem, const BigArgs& a, cudaStream_t s) {
+  if (grad) vecchia_big_kernel<true><<<blocks, threads, smem, s>>>(a);
+  else vecchia_big_kernel<false><<<blocks, threads, smem, s>>>(a);
 }
 
 }  // namespace vecchia

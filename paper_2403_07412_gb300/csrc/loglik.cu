@@ -34,8 +34,8 @@ struct BigArgs {
   double* terms;
   unsigned long long* errloc;
 };
-int big_config(int K, bool grad, int* blocks, int* smem);
-void launch_big(bool grad, int blocks, int smem, const BigArgs& a, cudaStream_t s);
+int big_config(int K, bool grad, int* blocks, int* threads, int* smem);
+void launch_big(bool grad, int blocks, int threads, int smem, const BigArgs& a, cudaStream_t s);
 bool theta_ok_family(const double* th, int family);
 int launch_matern_table(double nu, double* tab, cudaStream_t stream);
 bool theta_ok(const double* th);
@@ -294,8 +294,8 @@ int launch_with(Plan* p, const double* y_dev, const double* theta, bool grad, co
 // Blocks beyond the warp kernels' size: one CTA per location (bigblock.cu).
 static int launch_big_loglik(Plan* p, const double* y_dev, const double* theta, bool grad, double* out_dev,
                              double* terms_dev, cudaStream_t stream) {
-  int blocks = 0, smem = 0;
-  int rc = big_config(p->m + 1, grad, &blocks, &smem);
+  int blocks = 0, threads = 0, smem = 0;
+  int rc = big_config(p->m + 1, grad, &blocks, &threads, &smem);
   if (rc) return rc;
   if (p->partial_cap < (int64_t)blocks * 4) {
     if (p->d_partial) cudaFree(p->d_partial);
@@ -324,7 +324,7 @@ static int launch_big_loglik(Plan* p, const double* y_dev, const double* theta, 
   a.partial = p->d_partial;
   a.terms = terms_dev;
   a.errloc = p->d_errloc;
-  launch_big(grad, blocks, smem, a, stream);
+  launch_big(grad, blocks, threads, smem, a, stream);
   VECCHIA_CUDA_TRY(cudaGetLastError());
   if (out_dev) {
     const double dbeta_div = p->family == kFamilyPowExp ? theta[2] : 1.0;
