@@ -215,7 +215,7 @@ int vecchia_loglik_batched(const vecchia_plan_t* plans, const double* const* y_d
  * that owns every device byte, or a runtime that must never trigger an allocation
  * while serving).  It has no counterpart in the paper.  It calls no cudaMalloc,
  * cudaFree or other allocating routine; its scratch (per-warp partial sums for at
- * most 4096 warps, an error slot and one covariance table, about 210 KB) is a
+ * most 4096 warps, an error slot and one covariance table, about 190 KB) is a
  * file-scope __device__ array that every GPU loading the library keeps until the
  * process exits.  The launch is capped at 4096 warps; the kernel strides over the
  * locations, so no n is too large for the scratch.

@@ -19,13 +19,11 @@ constexpr int kEHi = 20;
 constexpr int kSub = 4;
 constexpr int kDeg = 8;
 constexpr int kNInt = (kEHi - kELo) << kSub;
-// Per interval: FP64 {c0, c1, c2, c3, c4, 2 c2} and FP32
-// {c5, c6, c7, c8, 3c3, 4c4, 5c5, 6c6, 7c7, 8c8, 0, 0} (see matern.cuh).
-constexpr int kNDbl = 6;
-constexpr int kNFlt = 12;
-// Small-u constants stored after the FP64 coefficients: kind, nu, a1, G, b0, b1, I(0).
+// Per interval kIntWords 16-byte words of coefficients (layout in matern.cuh), then
+// kNConst doubles of small-u constants: kind, nu, a1, G, b0, b1, I(0).
+constexpr int kIntWords = 5;
 constexpr int kNConst = 8;
-constexpr size_t kTableBytes = sizeof(double) * (kNInt * kNDbl + kNConst) + sizeof(float) * kNInt * kNFlt;
+constexpr size_t kTableBytes = (size_t)16 * kIntWords * kNInt + sizeof(double) * kNConst;
 
 // Largest conditioning sets: overall (CTA-per-location kernel) and for the warp kernels.
 constexpr int kMaxM = VECCHIA_MAX_M;

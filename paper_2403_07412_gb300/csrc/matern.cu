@@ -46,7 +46,7 @@ __device__ double quad_I(double u, double nu) {
 // exponent (power exponential).
 __global__ void matern_const_kernel(double nu, int family, double* tab) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  double* c = tab + kNInt * kNDbl;
+  double* c = tab + 2 * kIntWords * kNInt;
   if (family == kFamilyPowExp) {
     c[0] = __longlong_as_double(3LL);
     c[1] = nu;
@@ -74,6 +74,43 @@ __global__ void matern_const_kernel(double nu, int family, double* tab) {
 
 // One block of 32 threads per interval.  Node values: the Matérn quadrature, or the
 // power exponential exp(-u^(alpha/2)) (u = (d / beta^(1/alpha))^2) evaluated directly.
+// One interval's coefficients in the layout rho_poly reads (matern.cuh): c0 in FP64;
+// c1..c4 and 3 c3 as float pairs (hi = nearest float, lo = nearest float to the rest);
+// c5..c8, 5 c5, 6 c6 as floats; all but c0 scaled by 2^S, |max(c1..c4)| 2^S in [1/2, 1),
+// so that the float parts keep their relative precision wherever rho is small.
+__device__ void split_float(double x, float* hl) {
+  hl[0] = (float)x;
+  hl[1] = (float)(x - (double)hl[0]);
+}
+
+__device__ void write_interval(const double* mono, float* w) {
+  double top = 0.0;
+  for (int k = 1; k <= 4; ++k) top = fmax(top, fabs(mono[k]));
+  int S = 0;
+  if (top > 0.0) {
+    frexp(top, &S);
+    S = -S;
+  }
+  double c[kDeg + 1];
+  for (int k = 1; k <= kDeg; ++k) c[k] = ldexp(mono[k], S);
+  const unsigned long long c0 = (unsigned long long)__double_as_longlong(mono[0]);
+  w[0] = __uint_as_float((unsigned)(c0 & 0xFFFFFFFFULL));
+  w[1] = __uint_as_float((unsigned)(c0 >> 32));
+  split_float(c[1], w + 2);
+  split_float(c[2], w + 4);
+  split_float(c[3], w + 6);
+  split_float(c[4], w + 8);
+  w[10] = (float)c[5];
+  w[11] = (float)c[6];
+  w[12] = (float)c[7];
+  w[13] = (float)c[8];
+  w[14] = __int_as_float(S);
+  w[15] = 0.0f;
+  split_float(3.0 * c[3], w + 16);
+  w[18] = (float)(5.0 * c[5]);
+  w[19] = (float)(6.0 * c[6]);
+}
+
 __global__ void matern_fit_kernel(double nu, int family, double* tab) {
   constexpr int N = kDeg + 1;
   __shared__ double f[N], cheb[N], mono[N], tm[N][N];
@@ -81,7 +118,7 @@ __global__ void matern_fit_kernel(double nu, int family, double* tab) {
   const int e = kELo + (idx >> kSub);
   const int j = idx & ((1 << kSub) - 1);
   const int tid = threadIdx.x;
-  const double I0 = tab[kNInt * kNDbl + 6];
+  const double I0 = tab[2 * kIntWords * kNInt + 6];
   const double scale = ldexp(1.0, e);
   const double mid = scale * (1.0 + (2.0 * j + 1.0) / (2.0 * (1 << kSub)));
   const double hw = scale / (2.0 * (1 << kSub));
@@ -113,16 +150,7 @@ __global__ void matern_fit_kernel(double nu, int family, double* tab) {
     mono[tid] = a;
   }
   __syncthreads();
-  if (tid == 0) {
-    double* d = tab + idx * kNDbl;
-    for (int k = 0; k <= 4; ++k) d[k] = mono[k];
-    d[5] = 2.0 * mono[2];
-    float* fl = reinterpret_cast<float*>(tab + kNInt * kNDbl + kNConst) + idx * kNFlt;
-    for (int k = 5; k <= 8; ++k) fl[k - 5] = (float)mono[k];
-    for (int k = 3; k <= 8; ++k) fl[4 + k - 3] = (float)(k * mono[k]);
-    fl[10] = 0.0f;
-    fl[11] = 0.0f;
-  }
+  if (tid == 0) write_interval(mono, reinterpret_cast<float*>(tab) + (size_t)idx * 4 * kIntWords);
 }
 
 // ------------------------------------------------------------------ table cache

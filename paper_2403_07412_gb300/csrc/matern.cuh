@@ -5,18 +5,18 @@
 // piecewise polynomials (built on the GPU by matern_fit_kernel, see matern.cu):
 //   u in [2^e (1 + j/16), 2^e (1 + (j+1)/16)),  e in [kELo, kEHi),  j in 0..15,
 //   t = 32 u / 2^e - 33 - 2j in [-1, 1),  rho ~ P(t) = sum_{k<=8} c_k t^k.
-// The interval index, t and u dt/du = 32 M (M = mantissa of u) come from the bits of
-// u with integer operations.  On GB300 an FP64 instruction costs as much as ~60 others,
-// so the polynomial is split by magnitude:
-//   P(t) = c0 + t(c1 + t(c2 + t(c3 + t(c4 + t T5(t))))),
-//   T5(t) = c5 + c6 t + c7 t^2 + c8 t^3 evaluated in FP32;
-//   P'(t) = c1 + t(2 c2 + t R(t)),  R(t) = 3 c3 + 4 c4 t + ... + 8 c8 t^5 in FP32.
-// Near the origin the coefficients shrink by ~1/66 per degree, so the FP32 part of rho
-// stays below FP64 rounding (measured against exact rational evaluation: within
-// 1.7e-16 absolute, as an all-FP64 Horner), and h keeps ~1e-9 relative accuracy where
-// rho > 1e-3 (a few 1e-9 below), far below 1e-10 of max |h| in absolute terms, which
-// is what the beta-gradient (a sum of h-weighted pair terms) needs.  FP32 results
-// re-enter FP64 by exact bit conversion.  Cost: 5 FP64 FMAs for rho, 3 more for h.
+// The interval index and t come from the bits of u with integer operations.  On GB300
+// an FP64 instruction occupies its pipe about 76 times as long as an FP32 one, so only
+// the constant term is added in FP64:
+//   P(t) = c0 + t q(t),  q(t) = c1 + t(c2 + t(c3 + t(c4 + t T5(t)))),
+//   T5(t) = c5 + c6 t + c7 t^2 + c8 t^3.
+// q and t q are evaluated in double-float arithmetic (pairs of floats with error-free
+// products and sums, about 2^-47 relative), the tail T5 in plain FP32, and the pair
+// (hi, lo) of t q re-enters FP64 by exact bit conversion: two FP64 additions per rho.
+// Since |t q| is at most ~|c1| (~1/30 of rho's scale), the result stays within FP64
+// rounding of rho.  h = u rho'(u) = 32 M P'(t) (M = mantissa of u) is formed the same
+// way with one FP64 addition.  The float coefficients carry a per-interval power-of-two
+// scale, so that they keep their relative precision where rho is tiny.
 // Below 2^kELo the expansion of rho at u = 0 is used; at and above 2^kEHi, rho = 0.
 #pragma once
 
@@ -31,11 +31,15 @@ struct MaternConst {
   double nu, a1, G, b0, b1;
 };
 
-__device__ __forceinline__ const double* table_d(const double* tab) { return tab; }
-__device__ __forceinline__ const double* table_c(const double* tab) { return tab + kNInt * kNDbl; }
-__device__ __forceinline__ const float* table_f(const double* tab) {
-  return reinterpret_cast<const float*>(tab + kNInt * kNDbl + kNConst);
+// Coefficient words of interval idx (kIntWords float4 each):
+//   w0: c0 (FP64, low word first), c1 hi, c1 lo     w1: c2 hi, c2 lo, c3 hi, c3 lo
+//   w2: c4 hi, c4 lo, c5, c6                         w3: c7, c8, S (int), 0
+//   w4: 3c3 hi, 3c3 lo, 5c5, 6c6
+// where every float is the coefficient times 2^S.
+__device__ __forceinline__ const float4* table_iv(const double* tab) {
+  return reinterpret_cast<const float4*>(tab);
 }
+__device__ __forceinline__ const double* table_c(const double* tab) { return tab + 2 * kIntWords * kNInt; }
 
 __device__ __forceinline__ MaternConst load_matern_const(const double* __restrict__ tab) {
   const double* c = table_c(tab);
@@ -49,41 +53,65 @@ __device__ __forceinline__ MaternConst load_matern_const(const double* __restric
   return mc;
 }
 
-// Exact float -> double without the FP64 pipe (F2F is an FP64-pipe instruction).
-// Zero and subnormal floats (below 1.2e-38 in magnitude) map to zero.
-__device__ __forceinline__ double f2d_exact(float f) {
+// f 2^adj as a double, exactly, with integer operations (0 for zero, subnormal f, or
+// a result below the normal range).
+__device__ __forceinline__ double f2d_scaled(float f, int adj) {
   const unsigned fb = __float_as_uint(f);
   const unsigned ab = fb & 0x7FFFFFFFu;
-  if (ab < 0x00800000u) return 0.0;
+  const int e = (int)(ab >> 23) + 896 + adj;
+  if (ab < 0x00800000u || e <= 0) return 0.0;
   const unsigned long long db = ((unsigned long long)(fb & 0x80000000u) << 32) |
-                                ((unsigned long long)((ab >> 23) + 896u) << 52) |
-                                ((unsigned long long)(ab & 0x7FFFFFu) << 29);
+                                ((unsigned long long)e << 52) | ((unsigned long long)(ab & 0x7FFFFFu) << 29);
   return __longlong_as_double((long long)db);
 }
 
-// Bits of u below the sub-interval index, and the local variable t = s 2^-kTBits with
-// s = those bits - 2^kTBits (|s| <= 2^kTBits), converted exactly with integer operations.
-constexpr int kFracBits = 52 - kSub;  // bits of u below the sub-interval index
-constexpr int kTBits = kFracBits - 1;
-__device__ __forceinline__ double local_t(long long fr) {
-  const long long s = fr - (1LL << kTBits);
-  if (s == 0) return 0.0;
-  const unsigned long long sign = s < 0 ? 0x8000000000000000ULL : 0ULL;
-  const unsigned long long a = (unsigned long long)(s < 0 ? -s : s);
-  const int lz = __clzll((long long)a);             // leading one at bit 63 - lz
-  const unsigned long long e = (unsigned long long)(1023 + (63 - lz) - kTBits);
-  const unsigned long long mant = (a << (lz + 1)) >> 12;
-  return __longlong_as_double((long long)(sign | (e << 52) | mant));
+// v 2^-24 as a float, exactly, for v < 2^24 (no int-to-float conversion instruction).
+__device__ __forceinline__ float u24_float(unsigned v) {
+  return (__uint_as_float(0x3F800000u | (v & 0x7FFFFFu)) - ((v >> 23) ? 0.0f : 1.0f)) * 0.5f;
 }
 
-// The same t in FP32 (23 leading bits), for the FP32 tails.
-__device__ __forceinline__ float local_t_f32(long long fr) {
-  return fmaf(__uint_as_float(0x3F800000u | (unsigned)(fr >> (kFracBits - 23))), 2.0f, -3.0f);
+// Bits of u below the sub-interval index: fr (kFracBits = 48 bits), t = fr 2^-47 - 1,
+// returned as an exact float pair th + tl (the leading 24 and the trailing 24 bits).
+constexpr int kFracBits = 52 - kSub;
+__device__ __forceinline__ void local_t_df(long long fr, float& th, float& tl) {
+  const unsigned hi = (unsigned)(fr >> 24);
+  th = __uint_as_float(0x3F800000u | (hi & 0x7FFFFFu)) - ((hi >> 23) ? 1.0f : 2.0f);
+  tl = u24_float((unsigned)fr & 0xFFFFFFu) * 0x1p-23f;
 }
 
-// u dt/du = 2^(kSub+1) M, M = mantissa of u in [1, 2): the exponent field set to 1023+kSub+1.
-__device__ __forceinline__ double u_dtdu(long long b) {
-  return __longlong_as_double(((long long)(1023 + kSub + 1) << 52) | (b & 0xFFFFFFFFFFFFFLL));
+// Double-float arithmetic (error-free transformations; the explicit _rn intrinsics keep
+// the compiler from fusing the steps whose rounding errors are being captured).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// (h, l) = (ah, al) * (bh, bl), dropping al bl.
+__device__ __forceinline__ void df_mul(float ah, float al, float bh, float bl, float& h, float& l) {
+  h = __fmul_rn(ah, bh);
+  float e = fmaf(ah, bh, -h);
+  e = fmaf(ah, bl, e);
+  l = fmaf(al, bh, e);
+}
+
+// (ph, pl) <- (ch, cl) + (ph, pl) (th, tl), renormalised.
+__device__ __forceinline__ void df_horner(float& ph, float& pl, float th, float tl, float ch, float cl) {
+  float xh, xl, s, e;
+  df_mul(ph, pl, th, tl, xh, xl);
+  two_sum(ch, xh, s, e);
+  e = __fadd_rn(e, __fadd_rn(xl, cl));
+  ph = __fadd_rn(s, e);
+  pl = __fsub_rn(e, __fsub_rn(ph, s));
+}
+
+// (ph, pl) = (ch, cl) + p th for a plain float p (the tail), renormalised.
+__device__ __forceinline__ void df_start(float& ph, float& pl, float p, float th, float ch, float cl) {
+  float s, e;
+  two_sum(ch, __fmul_rn(p, th), s, e);
+  e = __fadd_rn(e, cl);
+  ph = __fadd_rn(s, e);
+  pl = __fsub_rn(e, __fsub_rn(ph, s));
 }
 
 // Expansion of rho and h at u -> 0 (u < 2^kELo), from the series of x^nu K_nu(x):
@@ -121,63 +149,70 @@ static __device__ __noinline__ void rho_small(double u, const MaternConst& mc, d
 // Polynomial part of rho(u) (and h(u) = u rho'(u) when DERIV), branch-free: the
 // interval index is clamped, so u outside [2^kELo, 2^kEHi) gets a finite value that
 // rho_fix() then replaces.
+struct PolyArg {
+  long long b;
+  int idx;
+  float th, tl;
+};
+
+__device__ __forceinline__ PolyArg poly_arg(double u) {
+  PolyArg a;
+  a.b = __double_as_longlong(u);
+  const int ex = min(max((int)(a.b >> 52) - 1023, kELo), kEHi - 1);
+  a.idx = ((ex - kELo) << kSub) | (int)((a.b >> kFracBits) & ((1 << kSub) - 1));
+  local_t_df(a.b & ((1LL << kFracBits) - 1), a.th, a.tl);
+  return a;
+}
+
+// 32 M P'(t) at scale 2^S as a float pair (M = mantissa of u, leading 47 bits).
+__device__ __forceinline__ void h_pair(const PolyArg& a, const float4& w0, const float4& w1, const float4& w2,
+                                       const float4& w3, const float4& w4, float& hh, float& hl) {
+  // P'(t) = c1 + t(2c2 + t(3c3 + t(4c4 + t D5(t)))),  D5 = 5c5 + t(6c6 + t(7c7 + t 8c8))
+  const float d5 = fmaf(fmaf(fmaf(8.0f * w3.y, a.th, 7.0f * w3.x), a.th, w4.w), a.th, w4.z);
+  float qh, ql;
+  df_start(qh, ql, d5, a.th, 4.0f * w2.x, 4.0f * w2.y);
+  df_horner(qh, ql, a.th, a.tl, w4.x, w4.y);
+  df_horner(qh, ql, a.th, a.tl, 2.0f * w1.x, 2.0f * w1.y);
+  df_horner(qh, ql, a.th, a.tl, w0.z, w0.w);
+  const float mh = __uint_as_float(0x3F800000u | (unsigned)((a.b >> 29) & 0x7FFFFF));
+  const float ml = u24_float((unsigned)(a.b >> 5) & 0xFFFFFFu) * 0x1p-23f;
+  df_mul(qh, ql, mh, ml, hh, hl);
+}
+
 template <bool DERIV>
 __device__ __forceinline__ void rho_poly(double u, const double* __restrict__ tab, double& rho, double& h) {
-  const long long b = __double_as_longlong(u);
-  const int ex = min(max((int)(b >> 52) - 1023, kELo), kEHi - 1);
-  const int idx = ((ex - kELo) << kSub) | (int)((b >> kFracBits) & ((1 << kSub) - 1));
-  const long long fr = b & ((1LL << kFracBits) - 1);
-  const double t = local_t(fr);
-  const float tf = local_t_f32(fr);
-  const double2* __restrict__ cd = reinterpret_cast<const double2*>(table_d(tab) + idx * kNDbl);
-  const float4* __restrict__ cf = reinterpret_cast<const float4*>(table_f(tab) + idx * kNFlt);
-  const double2 c01 = __ldg(cd), c23 = __ldg(cd + 1), c4x = __ldg(cd + 2);
-  const float4 f0 = __ldg(cf);
-  const float t5 = fmaf(fmaf(fmaf(f0.w, tf, f0.z), tf, f0.y), tf, f0.x);
-  double p = f2d_exact(t5);
-  p = fma(p, t, c4x.x);
-  p = fma(p, t, c23.y);
-  p = fma(p, t, c23.x);
-  p = fma(p, t, c01.y);
-  rho = fma(p, t, c01.x);
+  const PolyArg a = poly_arg(u);
+  const float4* __restrict__ w = table_iv(tab) + a.idx * kIntWords;
+  const float4 w0 = __ldg(w), w1 = __ldg(w + 1), w2 = __ldg(w + 2), w3 = __ldg(w + 3);
+  const int S = __float_as_int(w3.z);
+  const float t5 = fmaf(fmaf(fmaf(w3.y, a.th, w3.x), a.th, w2.w), a.th, w2.z);
+  float ph, pl;
+  df_start(ph, pl, t5, a.th, w2.x, w2.y);
+  df_horner(ph, pl, a.th, a.tl, w1.z, w1.w);
+  df_horner(ph, pl, a.th, a.tl, w1.x, w1.y);
+  df_horner(ph, pl, a.th, a.tl, w0.z, w0.w);
+  float xh, xl;
+  df_mul(ph, pl, a.th, a.tl, xh, xl);
+  const double c0 = __hiloint2double(__float_as_int(w0.y), __float_as_int(w0.x));
+  rho = (c0 + f2d_scaled(xh, -S)) + f2d_scaled(xl, -S);
   if (DERIV) {
-    const float4 f1 = __ldg(cf + 1), f2 = __ldg(cf + 2);
-    // R(t) = 3c3 + 4c4 t + 5c5 t^2 + 6c6 t^3 + 7c7 t^4 + 8c8 t^5
-    float r = f2.y;
-    r = fmaf(r, tf, f2.x);
-    r = fmaf(r, tf, f1.w);
-    r = fmaf(r, tf, f1.z);
-    r = fmaf(r, tf, f1.y);
-    r = fmaf(r, tf, f1.x);
-    const double dq = fma(t, f2d_exact(r), c4x.y);
-    const double dp = fma(t, dq, c01.y);
-    h = u_dtdu(b) * dp;
+    const float4 w4 = __ldg(w + 4);
+    float hh, hl;
+    h_pair(a, w0, w1, w2, w3, w4, hh, hl);
+    h = f2d_scaled(hh, 5 - S) + f2d_scaled(hl, 5 - S);
   }
 }
 
 // h(u) = u rho'(u) alone (the derivative part of rho_poly<true>), branch-free.
 __device__ __forceinline__ double h_poly(double u, const double* __restrict__ tab) {
-  const long long b = __double_as_longlong(u);
-  const int ex = min(max((int)(b >> 52) - 1023, kELo), kEHi - 1);
-  const int idx = ((ex - kELo) << kSub) | (int)((b >> kFracBits) & ((1 << kSub) - 1));
-  const long long fr = b & ((1LL << kFracBits) - 1);
-  const double t = local_t(fr);
-  const float tf = local_t_f32(fr);
-  const double2* __restrict__ cd = reinterpret_cast<const double2*>(table_d(tab) + idx * kNDbl);
-  const float4* __restrict__ cf = reinterpret_cast<const float4*>(table_f(tab) + idx * kNFlt);
-  const double2 c01 = __ldg(cd), c4x = __ldg(cd + 2);
-  const float4 f1 = __ldg(cf + 1), f2 = __ldg(cf + 2);
-  float r = f2.y;
-  r = fmaf(r, tf, f2.x);
-  r = fmaf(r, tf, f1.w);
-  r = fmaf(r, tf, f1.z);
-  r = fmaf(r, tf, f1.y);
-  r = fmaf(r, tf, f1.x);
-  const double dq = fma(t, f2d_exact(r), c4x.y);
-  const double dp = fma(t, dq, c01.y);
-  return u_dtdu(b) * dp;
+  const PolyArg a = poly_arg(u);
+  const float4* __restrict__ w = table_iv(tab) + a.idx * kIntWords;
+  const float4 w0 = __ldg(w), w1 = __ldg(w + 1), w2 = __ldg(w + 2), w3 = __ldg(w + 3), w4 = __ldg(w + 4);
+  const int S = __float_as_int(w3.z);
+  float hh, hl;
+  h_pair(a, w0, w1, w2, w3, w4, hh, hl);
+  return f2d_scaled(hh, 5 - S) + f2d_scaled(hl, 5 - S);
 }
-
 
 // Replaces rho_poly's value outside the tabulated range (rare): u < 2^kELo -> the
 // expansion at zero (Matérn) or direct evaluation (power exponential); u >= 2^kEHi ->
