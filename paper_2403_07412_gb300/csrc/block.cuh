@@ -58,7 +58,7 @@ struct SchedSize {
 // the adjoint, the weight vectors WH and GV.
 struct WarpArea {
   double *A, *YV, *TV, *WH, *GV;
-  long long *QX, *QY;
+  float2 *CX, *CY;
   __host__ __device__ static int doubles(int K, bool grad) {
     const SchedSize S(K);
     int d = align_up(S.NT, 2) + 4 * align_up(K + 1, 2);
@@ -68,9 +68,9 @@ struct WarpArea {
   __device__ WarpArea(double* base, int K) {
     const SchedSize S(K);
     A = base;
-    QX = reinterpret_cast<long long*>(A + align_up(S.NT, 2));
-    QY = QX + align_up(K + 1, 2);
-    YV = reinterpret_cast<double*>(QY + align_up(K + 1, 2));
+    CX = reinterpret_cast<float2*>(A + align_up(S.NT, 2));
+    CY = CX + align_up(K + 1, 2);
+    YV = reinterpret_cast<double*>(CY + align_up(K + 1, 2));
     TV = YV + align_up(K + 1, 2);
     WH = TV + align_up(K + 1, 2);
     GV = WH + align_up(K + 1, 2);
@@ -212,6 +212,69 @@ __device__ __forceinline__ double group_sum(double v) {
 // leaves early; inactive groups (active = false) compute a valid location and discard
 // it.  When terms_mode (the same for the whole warp), terms (if not null) receives l_i,
 // or {l_i, dl_i/dsigma2, dl_i/dbeta, dl_i/dtau2} when GRAD.  A block that is not positive definite gives a NaN term and records i in errloc.
+// x as a float pair hi + lo (hi: x's leading 24 bits, lo: the next 24, about 2^-48
+// relative), with integer operations; exponents far from 0 take the FP64 route.
+__device__ __forceinline__ float2 d2f_pair(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7FF) - 1023;
+  if (e < -90 || e > 90) {
+    const float hi = __double2float_rn(x);
+    return make_float2(hi, __double2float_rn(x - (double)hi));
+  }
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const float hi = __uint_as_float(sign | ((unsigned)(e + 127) << 23) | (unsigned)((b >> 29) & 0x7FFFFFu));
+  // remainder: mantissa bits 28..5, v 2^(e-47) = (v 2^-24) 2^(e-23)
+  const float lo = fscale(u24_float((unsigned)(b >> 5) & 0xFFFFFFu), e - 23);
+  return make_float2(hi, __uint_as_float(__float_as_uint(lo) | sign));
+}
+
+// Squared distance of two block points held as float pairs (x = hi + lo, about 2^-48
+// relative), in double-float arithmetic on the FP32 pipe: (uh, ul) within about 2^-46
+// of |p_r - p_c|^2 relative, plus 2^-47 of the block's coordinate scale in |p_r - p_c|.
+// A covariance entry needs absolute accuracy, and |drho/du| |du| stays far below the
+// factorisation's own rounding.  (An exact 128-bit fixed-point square costs ~70 integer
+// instructions at half rate; this costs ~41 full-rate FP32 ones.)
+__device__ __forceinline__ void df_diff(float2 a, float2 b, float& h, float& l) {
+  float s, e;
+  two_sum(a.x, -b.x, s, e);
+  e = __fadd_rn(e, __fsub_rn(a.y, b.y));
+  h = __fadd_rn(s, e);
+  l = __fsub_rn(e, __fsub_rn(h, s));
+}
+
+__device__ __forceinline__ void sq_dist_df(float2 xr, float2 xc, float2 yr, float2 yc, float& uh, float& ul) {
+  float dxh, dxl, dyh, dyl;
+  df_diff(xr, xc, dxh, dxl);
+  df_diff(yr, yc, dyh, dyl);
+  const float px = __fmul_rn(dxh, dxh), py = __fmul_rn(dyh, dyh);
+  float ex = fmaf(dxh, dxh, -px), ey = fmaf(dyh, dyh, -py);
+  ex = fmaf(dxh + dxh, dxl, ex);
+  ey = fmaf(dyh + dyh, dyl, ey);
+  float s, e;
+  two_sum(px, py, s, e);
+  e = __fadd_rn(e, __fadd_rn(ex, ey));
+  uh = __fadd_rn(s, e);
+  ul = __fsub_rn(e, __fsub_rn(uh, s));
+}
+
+// (pbh, pbl) += h (w_r g_c + w_c g_r) in double-float arithmetic.
+__device__ __forceinline__ void beta_pair_add(float2 wr, float2 wc, float2 gr, float2 gc, float hh, float hl,
+                                              float& pbh, float& pbl) {
+  float ah, al, bh, bl, s, e;
+  df_mul(wr.x, wr.y, gc.x, gc.y, ah, al);
+  df_mul(wc.x, wc.y, gr.x, gr.y, bh, bl);
+  two_sum(ah, bh, s, e);
+  e = __fadd_rn(e, __fadd_rn(al, bl));
+  const float th = __fadd_rn(s, e);
+  const float tl = __fsub_rn(e, __fsub_rn(th, s));
+  float ph, pl;
+  df_mul(hh, hl, th, tl, ph, pl);
+  two_sum(pbh, ph, s, e);
+  e = __fadd_rn(e, __fadd_rn(pl, pbl));
+  pbh = __fadd_rn(s, e);
+  pbl = __fsub_rn(e, __fsub_rn(pbh, s));
+}
+
 template <bool GRAD, int G>
 __device__ __forceinline__ void process_location(int64_t i, bool active, const FieldView& F, const SchedSize& S,
                                                  const uint16_t* __restrict__ sched,
@@ -223,50 +286,35 @@ __device__ __forceinline__ void process_location(int64_t i, bool active, const F
   const int m = F.m;
   const int K = m + 1;
   double* __restrict__ A = W.A;
-  long long* __restrict__ QX = W.QX;
-  long long* __restrict__ QY = W.QY;
+  float2* __restrict__ CX = W.CX;
+  float2* __restrict__ CY = W.CY;
   double* __restrict__ YV = W.YV;
   double* __restrict__ TV = W.TV;
   const int mi = i < m ? (int)i : m;
   const int32_t* __restrict__ row = F.nbr + i * m;
   const int js = F.self[i];
   const double2 ps = F.xy[js];
-  // ---- gather: centred, 1/beta-scaled coordinates (then fixed point) and data
-  double xv[NSG], yv[NSG];
-  int emax = 0;
+  // ---- gather: centred, 1/beta-scaled coordinates (as float pairs) and data
 #pragma unroll
   for (int s = 0; s < NSG; ++s) {
     const int p = sub + G * s;
-    xv[s] = 0.0;
-    yv[s] = 0.0;
     if (p < m) {
-      double fv = 0.0;
+      double xv = 0.0, yv = 0.0, fv = 0.0;
       if (p < mi) {
         const int j = row[p];
         const double2 q = F.xy[j];
-        xv[s] = (q.x - ps.x) * tc.inv_len;
-        yv[s] = (q.y - ps.y) * tc.inv_len;
+        xv = (q.x - ps.x) * tc.inv_len;
+        yv = (q.y - ps.y) * tc.inv_len;
         fv = F.yf[j];
       }
       YV[p] = fv;
-      emax = max(emax, (int)((__double_as_longlong(xv[s]) >> 52) & 0x7FF));
-      emax = max(emax, (int)((__double_as_longlong(yv[s]) >> 52) & 0x7FF));
-    }
-  }
-#pragma unroll
-  for (int o = G / 2; o > 0; o >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o, G));
-  const int FX = emax == 0 ? 0 : 61 - (emax - 1023);  // |coordinate| 2^FX < 2^62
-#pragma unroll
-  for (int s = 0; s < NSG; ++s) {
-    const int p = sub + G * s;
-    if (p < m) {
-      QX[p] = to_fixed(xv[s], FX);
-      QY[p] = to_fixed(yv[s], FX);
+      CX[p] = d2f_pair(xv);
+      CY[p] = d2f_pair(yv);
     }
   }
   if (sub == 0) {
-    QX[m] = 0;
-    QY[m] = 0;
+    CX[m] = make_float2(0.0f, 0.0f);
+    CY[m] = make_float2(0.0f, 0.0f);
     YV[m] = F.yf[js];
   }
   __syncwarp();
@@ -287,13 +335,10 @@ __device__ __forceinline__ void process_location(int64_t i, bool active, const F
     const int r1 = w1 & 0xFF, c1 = (w1 >> 8) & 0xFF;
     const bool v0 = c0 < mi && (r0 < mi || r0 == m);
     const bool v1 = has1 && c1 < mi && (r1 < mi || r1 == m);
-    const double u0 = fixed_sq_dist(QX[r0] - QX[c0], QY[r0] - QY[c0], FX);
-    const double u1 = fixed_sq_dist(QX[r1] - QX[c1], QY[r1] - QY[c1], FX);
-    double val0, hv0, val1, hv1;
-    rho_poly<false>(u0, tab, val0, hv0);
-    rho_poly<false>(u1, tab, val1, hv1);
-    rho_fix(u0, mc, val0, hv0);
-    rho_fix(u1, mc, val1, hv1);
+    float u0h, u0l, u1h, u1l;
+    sq_dist_df(CX[r0], CX[c0], CY[r0], CY[c0], u0h, u0l);
+    sq_dist_df(CX[r1], CX[c1], CY[r1], CY[c1], u1h, u1l);
+    const double val0 = rho_df(u0h, u0l, tab, mc), val1 = rho_df(u1h, u1l, tab, mc);
     A[w0 >> 16] = v0 ? val0 : 0.0;
     if (has1) A[w1 >> 16] = v1 ? val1 : 0.0;
   }
@@ -417,27 +462,31 @@ __device__ __forceinline__ void process_location(int64_t i, bool active, const F
   const double rs = rr * inv_s;
   const double cb = 0.5 * (rs * rs - inv_s);
   const double rsa = rs * tc.inv_sigma2;  // alpha = alpha~ / sigma2
+  // w^ and g are kept as float pairs for the beta pair sums below (double-float products
+  // there: the same ~2^-46 relative precision as h(u) itself, and no FP64 instruction).
+  float2* __restrict__ WHf = reinterpret_cast<float2*>(WH);
+  float2* __restrict__ GVf = reinterpret_cast<float2*>(GV);
   double pT = 0.0;
 #pragma unroll
   for (int t = 0; t < NS; ++t) {
     const int c = sub + G * t;
     if (c < K - 1) {
       const double wh = -w[t], gv = fma(rsa, bv[t], cb * wh);
-      WH[c] = wh;
-      GV[c] = gv;
+      WHf[c] = d2f_pair(wh);
+      GVf[c] = d2f_pair(gv);
       pT = fma(wh, gv, pT);
     }
   }
   if (sub == 0) {
-    WH[m] = 1.0;
-    GV[m] = cb;
+    WHf[m] = make_float2(1.0f, 0.0f);
+    GVf[m] = d2f_pair(cb);
     pT += cb;
   }
   const double sS = 0.5 * (rr * rs - 1.0);
   __syncwarp();
   // beta pair sums: h(u_pq) recomputed from the fixed-point coordinates (pads carry
   // zero weights), two pairs per iteration.
-  double pB = 0.0;
+  float pbh = 0.0f, pbl = 0.0f;
   for (int q0 = sub; q0 < S.NP; q0 += 2 * G) {
     const int q1 = q0 + G;
     const bool has1 = q1 < S.NP;
@@ -445,19 +494,16 @@ __device__ __forceinline__ void process_location(int64_t i, bool active, const F
     const uint32_t w1 = has1 ? pairs[q1] : w0;
     const int r0 = w0 & 0xFF, c0 = (w0 >> 8) & 0xFF;
     const int r1 = w1 & 0xFF, c1 = (w1 >> 8) & 0xFF;
-    const double u0 = fixed_sq_dist(QX[r0] - QX[c0], QY[r0] - QY[c0], FX);
-    const double u1 = fixed_sq_dist(QX[r1] - QX[c1], QY[r1] - QY[c1], FX);
-    const double h0 = h_fix(u0, mc, h_poly(u0, tab));
-    const double h1 = h_fix(u1, mc, h_poly(u1, tab));
-    double t0 = WH[r0] * GV[c0];
-    t0 = fma(WH[c0], GV[r0], t0);
-    pB = fma(h0, t0, pB);
-    if (has1) {
-      double t1 = WH[r1] * GV[c1];
-      t1 = fma(WH[c1], GV[r1], t1);
-      pB = fma(h1, t1, pB);
-    }
+    float u0h, u0l, u1h, u1l;
+    sq_dist_df(CX[r0], CX[c0], CY[r0], CY[c0], u0h, u0l);
+    sq_dist_df(CX[r1], CX[c1], CY[r1], CY[c1], u1h, u1l);
+    float h0h, h0l, h1h, h1l;
+    h_df(u0h, u0l, tab, mc, h0h, h0l);
+    h_df(u1h, u1l, tab, mc, h1h, h1l);
+    beta_pair_add(WHf[r0], WHf[c0], GVf[r0], GVf[c0], h0h, h0l, pbh, pbl);
+    if (has1) beta_pair_add(WHf[r1], WHf[c1], GVf[r1], GVf[c1], h1h, h1l, pbh, pbl);
   }
+  const double pB = f2d_scaled(pbh, 0) + f2d_scaled(pbl, 0);
   if (terms_mode) {
     const double tB = group_sum<G>(pB), tT = group_sum<G>(pT);
     if (terms && active && sub == 0) {

@@ -74,10 +74,10 @@ __global__ void matern_const_kernel(double nu, int family, double* tab) {
 
 // One block of 32 threads per interval.  Node values: the Matérn quadrature, or the
 // power exponential exp(-u^(alpha/2)) (u = (d / beta^(1/alpha))^2) evaluated directly.
-// One interval's coefficients in the layout rho_poly reads (matern.cuh): c0 in FP64;
-// c1..c4 and 3 c3 as float pairs (hi = nearest float, lo = nearest float to the rest);
-// c5..c8, 5 c5, 6 c6 as floats; all but c0 scaled by 2^S, |max(c1..c4)| 2^S in [1/2, 1),
-// so that the float parts keep their relative precision wherever rho is small.
+// One interval's coefficients in the layout of matern.cuh: c0 in FP64; c1..c4 and
+// 3 c3 as float pairs (hi = nearest float, lo = nearest float to the rest); c5..c8,
+// 5 c5, 6 c6 as floats; all floats scaled by 2^S, |max(c1..c4)| 2^S in [1/2, 1), so
+// that they keep their relative precision wherever rho is small.
 __device__ void split_float(double x, float* hl) {
   hl[0] = (float)x;
   hl[1] = (float)(x - (double)hl[0]);
@@ -93,17 +93,14 @@ __device__ void write_interval(const double* mono, float* w) {
   }
   double c[kDeg + 1];
   for (int k = 1; k <= kDeg; ++k) c[k] = ldexp(mono[k], S);
-  const unsigned long long c0 = (unsigned long long)__double_as_longlong(mono[0]);
-  w[0] = __uint_as_float((unsigned)(c0 & 0xFFFFFFFFULL));
-  w[1] = __uint_as_float((unsigned)(c0 >> 32));
-  split_float(c[1], w + 2);
-  split_float(c[2], w + 4);
-  split_float(c[3], w + 6);
-  split_float(c[4], w + 8);
-  w[10] = (float)c[5];
-  w[11] = (float)c[6];
-  w[12] = (float)c[7];
-  w[13] = (float)c[8];
+  split_float(c[1], w + 0);
+  split_float(c[2], w + 2);
+  split_float(c[3], w + 4);
+  split_float(c[4], w + 6);
+  for (int k = 5; k <= 8; ++k) w[8 + k - 5] = (float)c[k];
+  const unsigned long long d0 = (unsigned long long)__double_as_longlong(mono[0]);
+  w[12] = __uint_as_float((unsigned)(d0 & 0xFFFFFFFFULL));
+  w[13] = __uint_as_float((unsigned)(d0 >> 32));
   w[14] = __int_as_float(S);
   w[15] = 0.0f;
   split_float(3.0 * c[3], w + 16);

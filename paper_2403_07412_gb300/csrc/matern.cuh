@@ -31,11 +31,10 @@ struct MaternConst {
   double nu, a1, G, b0, b1;
 };
 
-// Coefficient words of interval idx (kIntWords float4 each):
-//   w0: c0 (FP64, low word first), c1 hi, c1 lo     w1: c2 hi, c2 lo, c3 hi, c3 lo
-//   w2: c4 hi, c4 lo, c5, c6                         w3: c7, c8, S (int), 0
+// Coefficient words of interval idx (kIntWords float4 each), every float times 2^S:
+//   w0: c1 hi, c1 lo, c2 hi, c2 lo      w1: c3 hi, c3 lo, c4 hi, c4 lo
+//   w2: c5, c6, c7, c8                   w3: c0 (FP64, low word first), S (int), 0
 //   w4: 3c3 hi, 3c3 lo, 5c5, 6c6
-// where every float is the coefficient times 2^S.
 __device__ __forceinline__ const float4* table_iv(const double* tab) {
   return reinterpret_cast<const float4*>(tab);
 }
@@ -166,51 +165,59 @@ __device__ __forceinline__ PolyArg poly_arg(double u) {
 
 // 32 M P'(t) at scale 2^S as a float pair (M = mantissa of u, leading 47 bits).
 __device__ __forceinline__ void h_pair(const PolyArg& a, const float4& w0, const float4& w1, const float4& w2,
-                                       const float4& w3, const float4& w4, float& hh, float& hl) {
+                                       const float4& w4, float& hh, float& hl) {
   // P'(t) = c1 + t(2c2 + t(3c3 + t(4c4 + t D5(t)))),  D5 = 5c5 + t(6c6 + t(7c7 + t 8c8))
-  const float d5 = fmaf(fmaf(fmaf(8.0f * w3.y, a.th, 7.0f * w3.x), a.th, w4.w), a.th, w4.z);
+  const float d5 = fmaf(fmaf(fmaf(8.0f * w2.w, a.th, 7.0f * w2.z), a.th, w4.w), a.th, w4.z);
   float qh, ql;
-  df_start(qh, ql, d5, a.th, 4.0f * w2.x, 4.0f * w2.y);
+  df_start(qh, ql, d5, a.th, 4.0f * w1.z, 4.0f * w1.w);
   df_horner(qh, ql, a.th, a.tl, w4.x, w4.y);
-  df_horner(qh, ql, a.th, a.tl, 2.0f * w1.x, 2.0f * w1.y);
-  df_horner(qh, ql, a.th, a.tl, w0.z, w0.w);
+  df_horner(qh, ql, a.th, a.tl, 2.0f * w0.z, 2.0f * w0.w);
+  df_horner(qh, ql, a.th, a.tl, w0.x, w0.y);
   const float mh = __uint_as_float(0x3F800000u | (unsigned)((a.b >> 29) & 0x7FFFFF));
   const float ml = u24_float((unsigned)(a.b >> 5) & 0xFFFFFFu) * 0x1p-23f;
   df_mul(qh, ql, mh, ml, hh, hl);
 }
 
+// t q(t) at scale 2^S as a float pair: the non-constant part of P(t).
+__device__ __forceinline__ void tq_pair(const PolyArg& a, const float4& w0, const float4& w1, const float4& w2,
+                                        float& xh, float& xl) {
+  const float t5 = fmaf(fmaf(fmaf(w2.w, a.th, w2.z), a.th, w2.y), a.th, w2.x);
+  float ph, pl;
+  df_start(ph, pl, t5, a.th, w1.z, w1.w);
+  df_horner(ph, pl, a.th, a.tl, w1.x, w1.y);
+  df_horner(ph, pl, a.th, a.tl, w0.z, w0.w);
+  df_horner(ph, pl, a.th, a.tl, w0.x, w0.y);
+  df_mul(ph, pl, a.th, a.tl, xh, xl);
+}
+
+// rho (and h when DERIV) to about FP64 rounding, relative, even where rho is tiny: c0 in
+// FP64 plus the pair, two FP64 additions for rho and one for h.
 template <bool DERIV>
 __device__ __forceinline__ void rho_poly(double u, const double* __restrict__ tab, double& rho, double& h) {
   const PolyArg a = poly_arg(u);
   const float4* __restrict__ w = table_iv(tab) + a.idx * kIntWords;
   const float4 w0 = __ldg(w), w1 = __ldg(w + 1), w2 = __ldg(w + 2), w3 = __ldg(w + 3);
   const int S = __float_as_int(w3.z);
-  const float t5 = fmaf(fmaf(fmaf(w3.y, a.th, w3.x), a.th, w2.w), a.th, w2.z);
-  float ph, pl;
-  df_start(ph, pl, t5, a.th, w2.x, w2.y);
-  df_horner(ph, pl, a.th, a.tl, w1.z, w1.w);
-  df_horner(ph, pl, a.th, a.tl, w1.x, w1.y);
-  df_horner(ph, pl, a.th, a.tl, w0.z, w0.w);
   float xh, xl;
-  df_mul(ph, pl, a.th, a.tl, xh, xl);
-  const double c0 = __hiloint2double(__float_as_int(w0.y), __float_as_int(w0.x));
+  tq_pair(a, w0, w1, w2, xh, xl);
+  const double c0 = __hiloint2double(__float_as_int(w3.y), __float_as_int(w3.x));
   rho = (c0 + f2d_scaled(xh, -S)) + f2d_scaled(xl, -S);
   if (DERIV) {
     const float4 w4 = __ldg(w + 4);
     float hh, hl;
-    h_pair(a, w0, w1, w2, w3, w4, hh, hl);
+    h_pair(a, w0, w1, w2, w4, hh, hl);
     h = f2d_scaled(hh, 5 - S) + f2d_scaled(hl, 5 - S);
   }
 }
 
-// h(u) = u rho'(u) alone (the derivative part of rho_poly<true>), branch-free.
+// h(u) = u rho'(u) alone in FP64 (one FP64 addition), branch-free.
 __device__ __forceinline__ double h_poly(double u, const double* __restrict__ tab) {
   const PolyArg a = poly_arg(u);
   const float4* __restrict__ w = table_iv(tab) + a.idx * kIntWords;
   const float4 w0 = __ldg(w), w1 = __ldg(w + 1), w2 = __ldg(w + 2), w3 = __ldg(w + 3), w4 = __ldg(w + 4);
   const int S = __float_as_int(w3.z);
   float hh, hl;
-  h_pair(a, w0, w1, w2, w3, w4, hh, hl);
+  h_pair(a, w0, w1, w2, w4, hh, hl);
   return f2d_scaled(hh, 5 - S) + f2d_scaled(hl, 5 - S);
 }
 
@@ -235,6 +242,90 @@ __device__ __forceinline__ double h_fix(double u, const MaternConst& mc, double 
     rho_fix(u, mc, r, h);
   }
   return h;
+}
+
+// ---- evaluation from a double-float argument u = uh + ul (likelihood kernels)
+// The interval index and t come from uh's float bits: u / 2^e = 1.m, t = 32 u / 2^e -
+// 33 - 2j, so th = (m mod 2^19) 2^-18 - 1 exactly and tl = ul 2^(5-e); 32 M = u dt/du is
+// (uh, ul) 2^(5-e).  Outside [2^kELo, 2^kEHi) the clamped index gives a finite value that
+// the rare path below replaces.
+struct PolyArgF {
+  int idx, ex;
+  float th, tl, mh, ml;  // t and 32 M as float pairs
+};
+
+__device__ __forceinline__ PolyArgF poly_arg_df(float uh, float ul) {
+  PolyArgF a;
+  const unsigned ub = __float_as_uint(uh);
+  a.ex = (int)((ub >> 23) & 0xFF) - 127;
+  const int ec = min(max(a.ex, kELo), kEHi - 1);
+  a.idx = ((ec - kELo) << kSub) | (int)((ub >> 19) & ((1u << kSub) - 1));
+  a.th = fmaf(__uint_as_float(0x3F800000u | ((ub & 0x7FFFFu) << 4)), 2.0f, -3.0f);
+  const float sc = __uint_as_float((unsigned)(127 + 5 - ec) << 23);
+  a.tl = __fmul_rn(ul, sc);
+  a.mh = __fmul_rn(uh, sc);
+  a.ml = a.tl;
+  return a;
+}
+
+// u outside the tabulated range as a double (rare path).
+__device__ __forceinline__ double df_to_double(float uh, float ul) {
+  return f2d_scaled(uh, 0) + f2d_scaled(ul, 0);
+}
+
+__device__ __forceinline__ double rho_df(float uh, float ul, const double* __restrict__ tab, const MaternConst& mc) {
+  const PolyArgF a = poly_arg_df(uh, ul);
+  const float4* __restrict__ w = table_iv(tab) + a.idx * kIntWords;
+  const float4 w0 = __ldg(w), w1 = __ldg(w + 1), w2 = __ldg(w + 2), w3 = __ldg(w + 3);
+  const int S = __float_as_int(w3.z);
+  const float t5 = fmaf(fmaf(fmaf(w2.w, a.th, w2.z), a.th, w2.y), a.th, w2.x);
+  float ph, pl, xh, xl;
+  df_start(ph, pl, t5, a.th, w1.z, w1.w);
+  df_horner(ph, pl, a.th, a.tl, w1.x, w1.y);
+  df_horner(ph, pl, a.th, a.tl, w0.z, w0.w);
+  df_horner(ph, pl, a.th, a.tl, w0.x, w0.y);
+  df_mul(ph, pl, a.th, a.tl, xh, xl);
+  const double c0 = __hiloint2double(__float_as_int(w3.y), __float_as_int(w3.x));
+  double rho = (c0 + f2d_scaled(xh, -S)) + f2d_scaled(xl, -S);
+  if (a.ex < kELo || a.ex >= kEHi) {
+    double h = 0.0;
+    rho_fix(df_to_double(uh, ul), mc, rho, h);
+  }
+  return rho;
+}
+
+// f 2^k for a float, by its exponent field; 0 when the result falls below the normal
+// range (|h| is at most a few units, so it never overflows).
+__device__ __forceinline__ float fscale(float f, int k) {
+  const unsigned fb = __float_as_uint(f);
+  const int ne = (int)((fb >> 23) & 0xFF) + k;
+  if ((fb & 0x7F800000u) == 0u || ne <= 0) return 0.0f;
+  return __uint_as_float((fb & 0x807FFFFFu) | ((unsigned)ne << 23));
+}
+
+// h(u) as a float pair (about 2^-46 relative), no FP64 instruction on the common path.
+__device__ __forceinline__ void h_df(float uh, float ul, const double* __restrict__ tab, const MaternConst& mc,
+                                     float& hh, float& hl) {
+  const PolyArgF a = poly_arg_df(uh, ul);
+  const float4* __restrict__ w = table_iv(tab) + a.idx * kIntWords;
+  const float4 w0 = __ldg(w), w1 = __ldg(w + 1), w2 = __ldg(w + 2), w3 = __ldg(w + 3), w4 = __ldg(w + 4);
+  const int S = __float_as_int(w3.z);
+  const float d5 = fmaf(fmaf(fmaf(8.0f * w2.w, a.th, 7.0f * w2.z), a.th, w4.w), a.th, w4.z);
+  float qh, ql;
+  df_start(qh, ql, d5, a.th, 4.0f * w1.z, 4.0f * w1.w);
+  df_horner(qh, ql, a.th, a.tl, w4.x, w4.y);
+  df_horner(qh, ql, a.th, a.tl, 2.0f * w0.z, 2.0f * w0.w);
+  df_horner(qh, ql, a.th, a.tl, w0.x, w0.y);
+  df_mul(qh, ql, a.mh, a.ml, hh, hl);  // 32 M P'(t), times 2^S
+  hh = fscale(hh, -S);
+  hl = fscale(hl, -S);
+  if (a.ex < kELo || a.ex >= kEHi) {
+    double r = 0.0, h = 0.0;
+    rho_fix(df_to_double(uh, ul), mc, r, h);
+    const float hi = __double2float_rn(h);
+    hh = hi;
+    hl = __double2float_rn(h - (double)hi);
+  }
 }
 
 template <bool DERIV>
