@@ -61,14 +61,15 @@ __global__ void __launch_bounds__(kCtaThreadsMax) vecchia_big_kernel(const BigAr
   const int m = a.m, K = m + 1;
   const int NTd = (K + 1) * (K + 2) / 2, NP = K * (K - 1) / 2;
   double* A = reinterpret_cast<double*>(smem);
-  long long* QX = reinterpret_cast<long long*>(A + align_up(NTd, 2));
-  long long* QY = QX + align_up(K + 1, 2);
-  double* YV = reinterpret_cast<double*>(QY + align_up(K + 1, 2));
+  float2* CX = reinterpret_cast<float2*>(A + align_up(NTd, 2));
+  float2* CY = CX + align_up(K + 1, 2);
+  double* YV = reinterpret_cast<double*>(CY + align_up(K + 1, 2));
   double* TV = YV + align_up(K + 1, 2);
   double* WH = TV + align_up(K + 1, 2);
   double* GV = WH + align_up(K + 1, 2);
   double* red = GV + align_up(K + 1, 2);
-  int* ired = reinterpret_cast<int*>(red + 32);
+  float2* WHf = reinterpret_cast<float2*>(WH);  // w^ and g as float pairs for the beta sums
+  float2* GVf = reinterpret_cast<float2*>(GV);
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int NTH = blockDim.x;
   const MaternConst mc = load_matern_const(a.tab);
@@ -81,42 +82,28 @@ __global__ void __launch_bounds__(kCtaThreadsMax) vecchia_big_kernel(const BigAr
     const int32_t* __restrict__ row = a.nbr + i * m;
     const int js = a.self[i];
     const double2 ps = xy2[js];
-    // ---- gather (two slots per thread covers m <= 2 * kCtaThreads)
-    double xv[2] = {0.0, 0.0}, yv[2] = {0.0, 0.0};
-    int emax = 0;
+    // ---- gather (two slots per thread covers m <= 2 * kCtaThreads): centred,
+    // 1/beta-scaled coordinates as float pairs, and data
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
       const int p = tid + NTH * s;
       if (p < m) {
-        double fv = 0.0;
+        double xv = 0.0, yv = 0.0, fv = 0.0;
         if (p < mi) {
           const int j = row[p];
           const double2 q = xy2[j];
-          xv[s] = (q.x - ps.x) * tc.inv_len;
-          yv[s] = (q.y - ps.y) * tc.inv_len;
+          xv = (q.x - ps.x) * tc.inv_len;
+          yv = (q.y - ps.y) * tc.inv_len;
           fv = a.yf[j];
         }
         YV[p] = fv;
-        emax = max(emax, (int)((__double_as_longlong(xv[s]) >> 52) & 0x7FF));
-        emax = max(emax, (int)((__double_as_longlong(yv[s]) >> 52) & 0x7FF));
-      }
-    }
-    emax = __reduce_max_sync(0xffffffffu, emax);
-    if (lane == 0) ired[wid] = emax;
-    __syncthreads();
-    for (int k = 0; k < NTH / 32; ++k) emax = max(emax, ired[k]);
-    const int FX = emax == 0 ? 0 : 61 - (emax - 1023);
-#pragma unroll
-    for (int s = 0; s < 2; ++s) {
-      const int p = tid + NTH * s;
-      if (p < m) {
-        QX[p] = to_fixed(xv[s], FX);
-        QY[p] = to_fixed(yv[s], FX);
+        CX[p] = d2f_pair(xv);
+        CY[p] = d2f_pair(yv);
       }
     }
     if (tid == 0) {
-      QX[m] = 0;
-      QY[m] = 0;
+      CX[m] = make_float2(0.0f, 0.0f);
+      CY[m] = make_float2(0.0f, 0.0f);
       YV[m] = a.yf[js];
     }
     __syncthreads();
@@ -136,13 +123,10 @@ __global__ void __launch_bounds__(kCtaThreadsMax) vecchia_big_kernel(const BigAr
       const int c1 = K - 2 - v1, r1 = c1 + 1 + (qq1 - v1 * (v1 + 1) / 2);
       const bool ok0 = c0 < mi && (r0 < mi || r0 == m);
       const bool ok1 = has1 && c1 < mi && (r1 < mi || r1 == m);
-      const double u0 = fixed_sq_dist(QX[r0] - QX[c0], QY[r0] - QY[c0], FX);
-      const double u1 = fixed_sq_dist(QX[r1] - QX[c1], QY[r1] - QY[c1], FX);
-      double val0, hv0, val1, hv1;
-      rho_poly<false>(u0, a.tab, val0, hv0);
-      rho_poly<false>(u1, a.tab, val1, hv1);
-      rho_fix(u0, mc, val0, hv0);
-      rho_fix(u1, mc, val1, hv1);
+      float u0h, u0l, u1h, u1l;
+      sq_dist_df(CX[r0], CX[c0], CY[r0], CY[c0], u0h, u0l);
+      sq_dist_df(CX[r1], CX[c1], CY[r1], CY[c1], u1h, u1l);
+      const double val0 = rho_df(u0h, u0l, a.tab, mc), val1 = rho_df(u1h, u1l, a.tab, mc);
       A[tri_off(K, c0) + r0 - c0] = ok0 ? val0 : 0.0;
       if (has1) A[tri_off(K, c1) + r1 - c1] = ok1 ? val1 : 0.0;
     }
@@ -251,30 +235,30 @@ __global__ void __launch_bounds__(kCtaThreadsMax) vecchia_big_kernel(const BigAr
         const int c = lane + 32 * t;
         if (c < K - 1) {
           const double wh = -w[t], gv = fma(rsa, bv[t], cb * wh);
-          WH[c] = wh;
-          GV[c] = gv;
+          WHf[c] = d2f_pair(wh);
+          GVf[c] = d2f_pair(gv);
           pT = fma(wh, gv, pT);
         }
       }
       if (lane == 0) {
-        WH[m] = 1.0;
-        GV[m] = cb;
+        WHf[m] = make_float2(1.0f, 0.0f);
+        GVf[m] = d2f_pair(cb);
         pT += cb;
       }
     }
     __syncthreads();
-    double pB = 0.0;
+    float pbh = 0.0f, pbl = 0.0f;
     if (good) {
       for (int q0 = tid; q0 < NP; q0 += NTH) {
         const int v0 = tri_root(q0);
         const int c0 = K - 2 - v0, r0 = c0 + 1 + (q0 - v0 * (v0 + 1) / 2);
-        const double u0 = fixed_sq_dist(QX[r0] - QX[c0], QY[r0] - QY[c0], FX);
-        const double h0 = h_fix(u0, mc, h_poly(u0, a.tab));
-        double t0 = WH[r0] * GV[c0];
-        t0 = fma(WH[c0], GV[r0], t0);
-        pB = fma(h0, t0, pB);
+        float uh, ul, hh, hl;
+        sq_dist_df(CX[r0], CX[c0], CY[r0], CY[c0], uh, ul);
+        h_df(uh, ul, a.tab, mc, hh, hl);
+        beta_pair_add(WHf[r0], WHf[c0], GVf[r0], GVf[c0], hh, hl, pbh, pbl);
       }
     }
+    const double pB = f2d_scaled(pbh, 0) + f2d_scaled(pbl, 0);
     const double sS = 0.5 * (rr * rs - 1.0);
     if (a.terms) {
       const double tB = block_sum(pB, red), tT = block_sum(pT, red);

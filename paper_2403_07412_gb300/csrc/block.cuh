@@ -54,16 +54,15 @@ struct SchedSize {
 };
 
 // Per-warp shared-memory area for blocks up to size K: the packed triangle A, the
-// block rows' fixed-point coordinates QX, QY and data YV, the pivot column TV and, for
-// the adjoint, the weight vectors WH and GV.
+// block rows' coordinates CX, CY (float pairs), the data YV (assembly only) and the
+// pivot column TV (elimination only).  The adjoint's weight vectors WH and GV reuse
+// YV and TV, so the gradient kernel fits as many warps per SM as the forward one.
 struct WarpArea {
   double *A, *YV, *TV, *WH, *GV;
   float2 *CX, *CY;
-  __host__ __device__ static int doubles(int K, bool grad) {
+  __host__ __device__ static int doubles(int K, bool /*grad*/) {
     const SchedSize S(K);
-    int d = align_up(S.NT, 2) + 4 * align_up(K + 1, 2);
-    if (grad) d += 2 * align_up(K + 1, 2);
-    return d;
+    return align_up(S.NT, 2) + 4 * align_up(K + 1, 2);
   }
   __device__ WarpArea(double* base, int K) {
     const SchedSize S(K);
@@ -72,62 +71,10 @@ struct WarpArea {
     CY = CX + align_up(K + 1, 2);
     YV = reinterpret_cast<double*>(CY + align_up(K + 1, 2));
     TV = YV + align_up(K + 1, 2);
-    WH = TV + align_up(K + 1, 2);
-    GV = WH + align_up(K + 1, 2);
+    WH = YV;
+    GV = TV;
   }
 };
-
-// Block coordinates as 64-bit fixed point: q = round(v 2^F), with F chosen per block so
-// that every |q| < 2^62.  Differences of fixed-point coordinates are then exact, and the
-// squared distance is formed in 128-bit integer arithmetic and rounded once to FP64:
-// no FP64 instruction per pair (an FP64 path would spend four).
-__device__ __forceinline__ long long to_fixed(double v, int F) {
-  const long long b = __double_as_longlong(v);
-  const int eb = (int)((b >> 52) & 0x7FF);
-  if (eb == 0) return 0;  // zero (or subnormal)
-  const long long mant = (b & 0xFFFFFFFFFFFFFLL) | (1LL << 52);
-  const int sh = eb - 1075 + F;  // v = mant 2^(eb-1075)
-  long long q;
-  if (sh >= 0) q = mant << sh;   // sh <= 9 for the block's largest coordinate
-  else if (sh > -63) q = (mant + (1LL << (-sh - 1))) >> (-sh);
-  else q = 0;
-  return b < 0 ? -q : q;
-}
-
-// (dx^2 + dy^2) 2^(-2F) for fixed-point differences |dx|, |dy| < 2^63, rounded to nearest.
-__device__ __forceinline__ double fixed_sq_dist(long long dx, long long dy, int F) {
-  const unsigned long long ax = (unsigned long long)(dx < 0 ? -dx : dx);
-  const unsigned long long ay = (unsigned long long)(dy < 0 ? -dy : dy);
-  const unsigned long long xl = ax * ax, yl = ay * ay;
-  const unsigned long long lo = xl + yl;
-  const unsigned long long hi = __umul64hi(ax, ax) + __umul64hi(ay, ay) + (lo < xl ? 1ULL : 0ULL);
-  if ((hi | lo) == 0ULL) return 0.0;
-  const int lz = hi ? __clzll((long long)hi) : 64 + __clzll((long long)lo);
-  unsigned long long nh, nl;  // normalised so the leading one is bit 127
-  if (lz >= 64) {
-    nh = lo << (lz - 64);
-    nl = 0ULL;
-  } else if (lz > 0) {
-    nh = (hi << lz) | (lo >> (64 - lz));
-    nl = lo << lz;
-  } else {
-    nh = hi;
-    nl = lo;
-  }
-  unsigned long long mant = nh >> 11;  // 53 bits with the leading one
-  const bool rbit = (nh >> 10) & 1ULL;
-  const bool sticky = (nh & 0x3FFULL) != 0ULL || nl != 0ULL;
-  if (rbit && (sticky || (mant & 1ULL))) mant += 1ULL;
-  int p = 127 - lz;
-  if (mant >> 53) {
-    mant >>= 1;
-    p += 1;
-  }
-  const int eb = 1023 + p - 2 * F;
-  if (eb <= 0) return 0.0;
-  if (eb >= 2047) return __longlong_as_double(0x7FF0000000000000LL);
-  return __longlong_as_double(((long long)eb << 52) | (long long)(mant & 0xFFFFFFFFFFFFFULL));
-}
 
 // Element schedules for block size K: sched[e] = (row, col) of packed slot e;
 // pairs[q] = (row, col, slot) of the q-th strictly-lower pair of the K x K block.
@@ -484,7 +431,7 @@ __device__ __forceinline__ void process_location(int64_t i, bool active, const F
   }
   const double sS = 0.5 * (rr * rs - 1.0);
   __syncwarp();
-  // beta pair sums: h(u_pq) recomputed from the fixed-point coordinates (pads carry
+  // beta pair sums: h(u_pq) recomputed from the float-pair coordinates (pads carry
   // zero weights), two pairs per iteration.
   float pbh = 0.0f, pbl = 0.0f;
   for (int q0 = sub; q0 < S.NP; q0 += 2 * G) {
