@@ -235,13 +235,31 @@ def cpu_baseline(xy, y, theta, m, budget_s):
     per_row = (time.perf_counter() - t0) / probe.size
     rows_n = int(max(64, min(200_000, budget_s / max(per_row, 1e-7))))
     rows = np.sort(rng.choice(np.arange(m + 1, n), rows_n, replace=False))
+    t0 = time.perf_counter()
     nb = oracle.knn_rows(xo, m, rows)
+    knn_s = time.perf_counter() - t0
     t0 = time.perf_counter()
     oracle.vecchia_rows(xo, yo, m, theta, rows=rows, nbr=nb, want_grad=True)
     dt = time.perf_counter() - t0
-    return {"value": rows_n / dt, "unit": "locations/s", "cores": oracle.num_threads(), "kind": "oracle",
+    cores = oracle.num_threads()
+    # one thread on a smaller slice of the same rows
+    one = rows[: max(16, rows_n // (4 * max(cores, 1)))]
+    oracle.set_threads(1)
+    t0 = time.perf_counter()
+    oracle.vecchia_rows(xo, yo, m, theta, rows=one, nbr=nb[: one.size], want_grad=True)
+    dt1 = time.perf_counter() - t0
+    oracle.set_threads(cores)
+    # the oracle's maxmin ordering on the first 100k locations of the workload
+    sub = xy[: min(n, 100_000)]
+    t0 = time.perf_counter()
+    oracle.order_maxmin(sub)
+    mm_s = time.perf_counter() - t0
+    return {"value": rows_n / dt, "unit": "locations/s", "cores": cores, "kind": "oracle",
             "sample": f"{rows_n} random locations (i > m) of the same 1M-location workload, loglik+grad, "
-                      f"oracle's own random ordering and brute-force neighbour sets (untimed); {dt:.1f} s wall"}
+                      f"oracle's own random ordering and brute-force neighbour sets (timed apart); {dt:.1f} s wall",
+            "single_thread": {"value": one.size / dt1, "unit": "locations/s", "sample": f"{one.size} of the same rows"},
+            "knn_rows_per_s": rows_n / knn_s,
+            "maxmin_100k_s": round(mm_s, 3)}
 
 
 def run_reference(args, rank, world):
@@ -436,6 +454,9 @@ def main():
                 traffic = tj.get(key)
         except Exception:
             traffic = None
+    hbm_gbs = traffic / (kern_ms * 1e-3) / 1e9 if traffic else None
+    cov_evals = float(sum(min(i, m) * (min(i, m) + 1) // 2 for i in range(min(n, m + 1)))) + \
+        float(max(n - (m + 1), 0)) * (m * (m + 1) // 2)
     line = {
         "metric": METRIC,
         "value": value,
@@ -464,6 +485,9 @@ def main():
                      "kernel": "vecchia_lik_kernel<true>" if not args.fwd else "vecchia_lik_kernel<false>",
                      "flops_per_launch": flops,
                      "peak_source": "FP64 DFMA-chain kernel measured in this run (vecchia_fp64_peak)"},
+        "covariance": {"entries_per_call": cov_evals, "entries_per_s": cov_evals / (kern_ms * 1e-3),
+                       "note": "off-diagonal covariance entries k(k-1)/2 per location, k = m_i + 1"},
+        "hbm": {"gbs": hbm_gbs, "source": "ncu dram bytes per launch (profiles/traffic.json) / CUDA-event time"},
         "e2e": {"value": world * n / (e2e_ms * 1e-3), "unit": "locations/s",
                 "h2d_bytes_per_step": int(y_host.numel() * 8), "d2h_bytes_per_step": int(res_host.numel() * 8)},
         "gpu_launches": 2 * args.steps,
