@@ -15,7 +15,10 @@ What each function follows:
   point from the point nearest the centroid, ties to the lowest index; Morton =
   Z-order of 16-bit cell indices).
 * :func:`knn_rows` — Algorithm 1, nearest-neighbour loop: the m nearest
-  *previously ordered* points, ties by index, brute force.
+  *previously ordered* points, ties by index, brute force; :func:`knn_rows_sphere`
+  the same on the sphere (keys: squared chord of unit vectors).
+* :func:`gcd` — Sec. VI-C great-circle distance (haversine); ``radius=`` switches
+  :func:`vecchia_rows` / :func:`loglik_exact` to it for (longitude, latitude) data.
 * :func:`vecchia_rows` / :func:`vecchia` — Sec. V-B: the Vecchia product of
   univariate conditionals, explicit conditional mean and variance, and the
   gradient in (sigma^2, beta, tau^2) by the joint-minus-marginal trace identity.
@@ -77,9 +80,12 @@ def _load():
             "oracle_order_morton": (c_int, [c_i64, _dp, _i64p]),
             "oracle_knn_rows": (c_int, [c_i64, _dp, c_i32, _i64p, c_i64, _i32p]),
             "oracle_vecchia_rows": (c_int, [c_i64, _dp, _dp, c_i32, _dp, _i64p, c_i64, _i32p, c_int,
-                                            _dp, _dp, _i64p, c_int]),
+                                            _dp, _dp, _i64p, c_int, c_int, c_d]),
+            "oracle_sphere_xyz": (None, [c_i64, _dp, _dp]),
+            "oracle_gcd": (None, [c_i64, _dp, _dp, c_d, _dp]),
+            "oracle_knn_rows_sphere": (c_int, [c_i64, _dp, c_i32, _i64p, c_i64, _i32p]),
             "oracle_sum_columns": (None, [c_i64, c_i32, _dp, _dp]),
-            "oracle_loglik_exact": (c_int, [c_i64, _dp, _dp, _dp, _dp, _dp, c_int]),
+            "oracle_loglik_exact": (c_int, [c_i64, _dp, _dp, _dp, _dp, _dp, c_int, c_int, c_d]),
             "oracle_block_logdensity": (c_int, [c_i32, _dp, _dp, _dp]),
         }
         for name, (res, args) in sig.items():
@@ -187,6 +193,35 @@ def knn_rows(xy_ordered, m: int, rows=None) -> np.ndarray:
     return out
 
 
+def sphere_xyz(lonlat) -> np.ndarray:
+    """Unit vectors (n x 3) of (longitude, latitude) points given in degrees."""
+    ll = _f64(lonlat).reshape(-1, 2)
+    out = np.empty((ll.shape[0], 3), dtype=np.float64)
+    _load().oracle_sphere_xyz(ll.shape[0], _p(ll, _dp), _p(out, _dp))
+    return out
+
+
+def gcd(a, b, radius: float) -> np.ndarray:
+    """Great-circle distances (Sec. VI-C, haversine) between rows of a and b (lon, lat degrees)."""
+    a = _f64(a).reshape(-1, 2)
+    b = _f64(b).reshape(-1, 2)
+    out = np.empty(a.shape[0], dtype=np.float64)
+    _load().oracle_gcd(a.shape[0], _p(a, _dp), _p(b, _dp), float(radius), _p(out, _dp))
+    return out
+
+
+def knn_rows_sphere(xyz_ordered, m: int, rows=None) -> np.ndarray:
+    """Conditioning sets on the sphere from ordered unit vectors, keys (chord^2, index)."""
+    xyz = _f64(xyz_ordered).reshape(-1, 3)
+    n = xyz.shape[0]
+    rows = np.arange(n, dtype=np.int64) if rows is None else np.ascontiguousarray(rows, dtype=np.int64)
+    out = np.empty((rows.size, m), dtype=np.int32)
+    rc = _load().oracle_knn_rows_sphere(n, _p(xyz, _dp), m, _p(rows, _i64p), rows.size, _p(out, _i32p))
+    if rc:
+        raise ValueError("oracle_knn_rows_sphere: invalid arguments")
+    return out
+
+
 class OracleNotPD(RuntimeError):
     def __init__(self, row):
         super().__init__(f"conditional block not positive definite at ordered location {row}")
@@ -194,19 +229,21 @@ class OracleNotPD(RuntimeError):
 
 
 def vecchia_rows(xy_ordered, y_ordered, m: int, theta, rows=None, nbr=None, want_grad=False,
-                 return_mu_s=False, family=0):
+                 return_mu_s=False, family=0, radius=None):
     """Per-location Vecchia terms (and gradients) for the given ordered rows.
 
     theta = (sigma2, beta, nu, tau2); family 0 = Matérn (Eq. 2), 1 = power exponential
-    (Eq. 3, nu = exponent).  Returns an array of shape (nrows,) or
-    (nrows, 4) = (l_i, dl_i/dsigma2, dl_i/dbeta, dl_i/dtau2).
+    (Eq. 3, nu = exponent).  With ``radius`` set, the points are (longitude, latitude)
+    in degrees and distances are great-circle distances on that sphere (Sec. VI-C).
+    Returns an array of shape (nrows,) or (nrows, 4) = (l_i, dl_i/dsigma2, dl_i/dbeta,
+    dl_i/dtau2).
     """
     xy = _f64(xy_ordered).reshape(-1, 2)
     y = _f64(y_ordered)
     n = xy.shape[0]
     rows = np.arange(n, dtype=np.int64) if rows is None else np.ascontiguousarray(rows, dtype=np.int64)
     if nbr is None:
-        nbr = knn_rows(xy, m, rows)
+        nbr = knn_rows(xy, m, rows) if radius is None else knn_rows_sphere(sphere_xyz(xy), m, rows)
     nbr = np.ascontiguousarray(nbr, dtype=np.int32)
     th = _f64(theta)
     w = 4 if want_grad else 1
@@ -215,7 +252,8 @@ def vecchia_rows(xy_ordered, y_ordered, m: int, theta, rows=None, nbr=None, want
     bad = np.full(1, -1, dtype=np.int64)
     rc = _load().oracle_vecchia_rows(n, _p(xy, _dp), _p(y, _dp), m, _p(th, _dp), _p(rows, _i64p),
                                      rows.size, _p(nbr, _i32p), 1 if want_grad else 0, _p(out, _dp),
-                                     _p(mu_s, _dp), _p(bad, _i64p), int(family))
+                                     _p(mu_s, _dp), _p(bad, _i64p), int(family),
+                                     0 if radius is None else 1, 0.0 if radius is None else float(radius))
     if rc:
         raise OracleNotPD(int(bad[0]))
     res = out if want_grad else out[:, 0]
@@ -232,22 +270,24 @@ def compensated_sum(v) -> np.ndarray:
     return out
 
 
-def vecchia(xy_ordered, y_ordered, m: int, theta, want_grad=False, family=0):
+def vecchia(xy_ordered, y_ordered, m: int, theta, want_grad=False, family=0, radius=None):
     """Vecchia log-likelihood over all ordered locations: l or (l, dsigma2, dbeta, dtau2)."""
-    terms = vecchia_rows(xy_ordered, y_ordered, m, theta, want_grad=want_grad, family=family)
+    terms = vecchia_rows(xy_ordered, y_ordered, m, theta, want_grad=want_grad, family=family, radius=radius)
     s = compensated_sum(terms)
     return s if want_grad else float(s[0])
 
 
-def loglik_exact(xy, y, theta, want_grad=False, family=0):
-    """Eq. (1): exact zero-mean Gaussian log-likelihood (dense, O(n^3))."""
+def loglik_exact(xy, y, theta, want_grad=False, family=0, radius=None):
+    """Eq. (1): exact zero-mean Gaussian log-likelihood (dense, O(n^3)); ``radius`` as in
+    :func:`vecchia_rows`."""
     xy = _f64(xy).reshape(-1, 2)
     y = _f64(y)
     th = _f64(theta)
     out = np.empty(1)
     g = np.empty(3)
     rc = _load().oracle_loglik_exact(xy.shape[0], _p(xy, _dp), _p(y, _dp), _p(th, _dp), _p(out, _dp),
-                                     _p(g, _dp) if want_grad else None, int(family))
+                                     _p(g, _dp) if want_grad else None, int(family),
+                                     0 if radius is None else 1, 0.0 if radius is None else float(radius))
     if rc:
         raise OracleNotPD(-1)
     return (float(out[0]), g) if want_grad else float(out[0])

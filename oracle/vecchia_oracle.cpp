@@ -15,6 +15,8 @@
 //   Algorithm 1: permutation, m nearest previously-ordered
 //   neighbours, conditional mean / variance, univariate terms     (Sec. V-B)
 //   Sec. V-A: random and maxmin orderings.
+//   Sec. VI-C: great-circle distance by the haversine formula (longitude/latitude
+//   data), used with a sphere of given radius.
 // Readings where the paper is silent (nugget, ties, maxmin start, short early
 // conditioning sets, splitmix64 Fisher–Yates) are listed in the design notes and
 // restated at each function below.
@@ -36,6 +38,7 @@
 namespace {
 
 constexpr double kLog2Pi = 1.8378770664093454835606594728112;  // log(2*pi)
+constexpr double kPi = 3.14159265358979323846;
 
 // ---------------------------------------------------------------- covariance
 // Eq. (2): C(d) = sigma2 * 2^(1-nu)/Gamma(nu) * (d/beta)^nu * K_nu(d/beta),
@@ -86,6 +89,52 @@ inline double dist2(const double* a, const double* b) {
   const double px = dx * dx;
   const double py = dy * dy;
   return px + py;
+}
+
+// Great-circle distance (Sec. VI-C): with latitudes phi and longitudes lambda in
+// radians, hav(d / r) = hav(phi2 - phi1) + cos(phi1) cos(phi2) hav(lambda2 - lambda1),
+// hav(x) = sin^2(x / 2), so d = 2 r asin(sqrt(h)).  Points are (longitude, latitude)
+// in degrees.
+double gcd(const double* a, const double* b, double radius) {
+  const double rad = kPi / 180.0;
+  const double p1 = a[1] * rad, p2 = b[1] * rad;
+  const double sp = std::sin(0.5 * (p2 - p1));
+  const double sl = std::sin(0.5 * (b[0] - a[0]) * rad);
+  double h = sp * sp + std::cos(p1) * std::cos(p2) * (sl * sl);
+  if (h > 1.0) h = 1.0;
+  return 2.0 * radius * std::asin(std::sqrt(h));
+}
+
+// Distance between points p and q: Euclidean in the plane (metric 0, pts n x 2 in the
+// plane) or great-circle on a sphere of the given radius (metric 1, pts n x 2 as
+// longitude/latitude in degrees).
+inline double point_dist(const double* pts, int64_t p, int64_t q, int metric, double radius) {
+  if (metric == 1) return gcd(pts + 2 * p, pts + 2 * q, radius);
+  return std::sqrt(dist2(pts + 2 * p, pts + 2 * q));
+}
+
+// Unit vector of a (longitude, latitude) point in degrees:
+// (cos(phi) cos(lambda), cos(phi) sin(lambda), sin(phi)).  The nearest-neighbour
+// search on the sphere ranks candidates by the squared chord between these vectors,
+// which increases with the great-circle distance (chord = 2 sin(d / 2r)).
+void unit_vector(const double* lonlat, double* out) {
+  const double rad = kPi / 180.0;
+  const double lam = lonlat[0] * rad, phi = lonlat[1] * rad;
+  const double cp = std::cos(phi);
+  out[0] = cp * std::cos(lam);
+  out[1] = cp * std::sin(lam);
+  out[2] = std::sin(phi);
+}
+
+// Squared chord, evaluated as round(round(round(dx*dx) + round(dy*dy)) + round(dz*dz)).
+inline double chord2(const double* a, const double* b) {
+  const double dx = a[0] - b[0];
+  const double dy = a[1] - b[1];
+  const double dz = a[2] - b[2];
+  const double px = dx * dx;
+  const double py = dy * dy;
+  const double pz = dz * dz;
+  return (px + py) + pz;
 }
 
 // ---------------------------------------------------------------- dense algebra
@@ -169,6 +218,25 @@ void knn_row(const double* xy, int64_t i, int m, int32_t* out) {
   for (int p = 0; p < m; ++p) out[p] = p < mi ? (int32_t)bj[p] : -1;
 }
 
+// The same search on the sphere: xyz are unit vectors (n x 3), keys (chord^2, index).
+void knn_row_sphere(const double* xyz, int64_t i, int m, int32_t* out) {
+  const int mi = (int)std::min<int64_t>(i, m);
+  std::vector<double> bd(mi);
+  std::vector<int64_t> bj(mi);
+  int cnt = 0;
+  for (int64_t j = 0; j < i; ++j) {
+    const double d = chord2(xyz + 3 * i, xyz + 3 * j);
+    if (cnt == mi) {
+      if (!(d < bd[mi - 1])) continue;
+      --cnt;
+    }
+    int p = cnt;
+    while (p > 0 && (d < bd[p - 1])) { bd[p] = bd[p - 1]; bj[p] = bj[p - 1]; --p; }
+    bd[p] = d; bj[p] = j; ++cnt;
+  }
+  for (int p = 0; p < m; ++p) out[p] = p < mi ? (int32_t)bj[p] : -1;
+}
+
 // ---------------------------------------------------------------- one location
 // Vecchia term for ordered location i with conditioning set J (Sec. V-B):
 //   mu_i = Sigma_iJ Sigma_JJ^{-1} y_J,   s_i = Sigma_ii - Sigma_iJ Sigma_JJ^{-1} Sigma_Ji,
@@ -180,7 +248,8 @@ void knn_row(const double* xy, int64_t i, int m, int32_t* out) {
 //   d log N(y; 0, S)/d theta_p = -1/2 tr(S^{-1} S_p) + 1/2 a^T S_p a,  a = S^{-1} y,
 // with S_sigma2 = (S - tau2 I)/sigma2, S_tau2 = I, S_beta = [dC/dbeta(d_pq)].
 int location_term(const double* xy, const double* y, int64_t i, const int32_t* J, int mi,
-                  const double* theta, int family, double* term, double* grad, double* mu_out, double* s_out) {
+                  const double* theta, int family, int metric, double radius, double* term, double* grad,
+                  double* mu_out, double* s_out) {
   const double sigma2 = theta[0], beta = theta[1], nu = theta[2], tau2 = theta[3];
   const int k = mi + 1;  // block B = J followed by i
   std::vector<int64_t> idx(k);
@@ -189,7 +258,7 @@ int location_term(const double* xy, const double* y, int64_t i, const int32_t* J
   std::vector<double> S((size_t)k * k), D((size_t)k * k);
   for (int p = 0; p < k; ++p) {
     for (int q = 0; q < k; ++q) {
-      const double d = std::sqrt(dist2(xy + 2 * idx[p], xy + 2 * idx[q]));
+      const double d = p == q ? 0.0 : point_dist(xy, idx[p], idx[q], metric, radius);
       S[(size_t)p * k + q] = (p == q ? sigma2 + tau2 : cov(family, d, sigma2, beta, nu));
       if (grad) D[(size_t)p * k + q] = (p == q ? 0.0 : cov_dbeta(family, d, sigma2, beta, nu));
     }
@@ -409,6 +478,27 @@ int oracle_knn_rows(int64_t n, const double* xy, int32_t m, const int64_t* rows,
   return 0;
 }
 
+// Unit vectors of n (longitude, latitude) points in degrees (n x 3 out).
+void oracle_sphere_xyz(int64_t n, const double* lonlat, double* xyz) {
+  for (int64_t i = 0; i < n; ++i) unit_vector(lonlat + 2 * i, xyz + 3 * i);
+}
+
+// Great-circle distances between n pairs of (longitude, latitude) points in degrees.
+void oracle_gcd(int64_t n, const double* a, const double* b, double radius, double* out) {
+  for (int64_t i = 0; i < n; ++i) out[i] = gcd(a + 2 * i, b + 2 * i, radius);
+}
+
+// Brute-force conditioning sets on the sphere for the listed ordered rows; xyz is the
+// ordered unit vectors (n x 3).
+int oracle_knn_rows_sphere(int64_t n, const double* xyz, int32_t m, const int64_t* rows, int64_t nrows,
+                           int32_t* out) {
+  if (m < 1) return 1;
+  for (int64_t r = 0; r < nrows; ++r) if (rows[r] < 0 || rows[r] >= n) return 1;
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t r = 0; r < nrows; ++r) knn_row_sphere(xyz, rows[r], m, out + (size_t)r * m);
+  return 0;
+}
+
 // Vecchia terms for the listed ordered rows, given their conditioning sets
 // (nbr: nrows x m, -1 padded, as produced by oracle_knn_rows).
 // out: nrows x (want_grad ? 4 : 1): (l_i[, dl_i/dsigma2, dl_i/dbeta, dl_i/dtau2]).
@@ -416,7 +506,7 @@ int oracle_knn_rows(int64_t n, const double* xy, int32_t m, const int64_t* rows,
 // bad_row (optional): first failing row index on a non-PD block.
 int oracle_vecchia_rows(int64_t n, const double* xy, const double* y, int32_t m, const double* theta,
                         const int64_t* rows, int64_t nrows, const int32_t* nbr, int want_grad,
-                        double* out, double* mu_s, int64_t* bad_row, int family) {
+                        double* out, double* mu_s, int64_t* bad_row, int family, int metric, double radius) {
   (void)n;
   const int w = want_grad ? 4 : 1;
   int64_t first_bad = -1;
@@ -427,7 +517,7 @@ int oracle_vecchia_rows(int64_t n, const double* xy, const double* y, int32_t m,
     while (mi < m && J[mi] >= 0) ++mi;
     double g[3];
     double mu = 0.0, s = 0.0;
-    const int rc = location_term(xy, y, rows[r], J, mi, theta, family, out + (size_t)r * w,
+    const int rc = location_term(xy, y, rows[r], J, mi, theta, family, metric, radius, out + (size_t)r * w,
                                  want_grad ? g : nullptr, &mu, &s);
     if (rc) {
 #pragma omp critical
@@ -454,13 +544,13 @@ void oracle_sum_columns(int64_t nrows, int32_t cols, const double* v, double* ou
 // tau2 delta_pq; O(n^3) with the oracle's own Cholesky.  grad (optional):
 // d l / d(sigma2, beta, tau2) by -1/2 tr(Sigma^{-1} Sigma_p) + 1/2 a^T Sigma_p a.
 int oracle_loglik_exact(int64_t n, const double* xy, const double* y, const double* theta,
-                        double* out, double* grad, int family) {
+                        double* out, double* grad, int family, int metric, double radius) {
   const double sigma2 = theta[0], beta = theta[1], nu = theta[2], tau2 = theta[3];
   const int k = (int)n;
   std::vector<double> S((size_t)k * k), L((size_t)k * k), a(k);
   for (int p = 0; p < k; ++p)
     for (int q = 0; q < k; ++q) {
-      const double d = std::sqrt(dist2(xy + 2 * p, xy + 2 * q));
+      const double d = p == q ? 0.0 : point_dist(xy, p, q, metric, radius);
       S[(size_t)p * k + q] = p == q ? sigma2 + tau2 : cov(family, d, sigma2, beta, nu);
     }
   if (!cholesky(k, S.data(), L.data())) return 2;
@@ -478,8 +568,7 @@ int oracle_loglik_exact(int64_t n, const double* xy, const double* y, const doub
         double Sp;
         if (t == 0) Sp = (S[(size_t)p * k + q] - (p == q ? tau2 : 0.0)) / sigma2;
         else if (t == 1) {
-          const double d = std::sqrt(dist2(xy + 2 * p, xy + 2 * q));
-          Sp = p == q ? 0.0 : cov_dbeta(family, d, sigma2, beta, nu);
+          Sp = p == q ? 0.0 : cov_dbeta(family, point_dist(xy, p, q, metric, radius), sigma2, beta, nu);
         } else Sp = p == q ? 1.0 : 0.0;
         tr += Si[(size_t)q * k + p] * Sp;
         qd += a[p] * Sp * a[q];

@@ -19,6 +19,11 @@ not available here, so seeded synthetic fields stand in for them):
   nugget noise, for large n.  The spectral density of
   C(d) ∝ (d/beta)^nu K_nu(d/beta) in 2-D is ∝ (beta^-2 + |w|^2)^-(nu+1); it is
   sampled as w = z / (beta sqrt(2 g)), z ~ N(0, I_2), g ~ Gamma(nu, 1).
+* ``sphere_locations``   — n (longitude, latitude) points in degrees, area-uniform
+  on a latitude/longitude patch (default: a 15 x 15 degree region like the paper's
+  Mississippi-basin soil data, Sec. VI-C).
+* ``sphere_coords``      — 3-D coordinates (radius x unit vector) of such points, so
+  that ``field_rff`` / ``field_dense`` draw fields in chordal distance on the sphere.
 * ``theta_candidates``   — parameter vectors for the many-field batched mode.
 """
 from __future__ import annotations
@@ -81,7 +86,7 @@ def field_rff(xy: np.ndarray, theta, seed: int, features: int = 4096, device=Non
     """
     sigma2, beta, nu, tau2 = (float(t) for t in theta)
     g = rng(seed)
-    z = g.standard_normal((features, 2))
+    z = g.standard_normal((features, xy.shape[1]))
     gam = g.gamma(nu, 1.0, size=features)
     w = z / (beta * np.sqrt(2.0 * gam))[:, None]
     b = g.uniform(0.0, 2.0 * np.pi, size=features)
@@ -102,6 +107,21 @@ def field_rff(xy: np.ndarray, theta, seed: int, features: int = 4096, device=Non
             p = xy[s:s + chunk // 16]
             f[s:s + chunk // 16] = np.cos(p @ w.T + b).sum(1) * amp
     return f + np.sqrt(tau2) * eps
+
+
+def sphere_locations(n: int, seed: int, lon=(-100.0, -85.0), lat=(30.0, 45.0)) -> np.ndarray:
+    """n (longitude, latitude) points in degrees, uniform in area on the patch."""
+    g = rng(seed)
+    lo = g.uniform(lon[0], lon[1], size=n)
+    s0, s1 = np.sin(np.radians(lat[0])), np.sin(np.radians(lat[1]))
+    la = np.degrees(np.arcsin(g.uniform(s0, s1, size=n)))
+    return np.stack([lo, la], axis=1)
+
+
+def sphere_coords(lonlat: np.ndarray, radius: float) -> np.ndarray:
+    """radius x unit vectors of (longitude, latitude) points (data generation only)."""
+    lam, phi = np.radians(lonlat[:, 0]), np.radians(lonlat[:, 1])
+    return radius * np.stack([np.cos(phi) * np.cos(lam), np.cos(phi) * np.sin(lam), np.sin(phi)], axis=1)
 
 
 def theta_candidates(nfields: int, ntheta: int, seed: int) -> np.ndarray:

@@ -331,3 +331,70 @@ def test_not_positive_definite_is_reported(oracle_mod):
     with pytest.raises(oracle_mod.OracleNotPD) as e:
         oracle_mod.vecchia_rows(xy, y, 2, (1.0, 0.1, 0.5, 0.0))
     assert e.value.row == 1
+
+
+# ----------------------------------------------------------------- Sec. VI-C: sphere
+R_EARTH = 6371.0
+
+
+def test_gcd_special_values(oracle_mod):
+    a = np.array([[0.0, 0.0], [0.0, 0.0], [0.0, 0.0], [10.0, 20.0], [-75.0, 40.0], [30.0, 89.0]])
+    b = np.array([[0.0, 90.0], [180.0, 0.0], [1.0, 0.0], [10.0, 20.0], [-75.0, 41.0], [210.0, 89.0]])
+    got = oracle_mod.gcd(a, b, R_EARTH)
+    want = R_EARTH * np.radians([90.0, 180.0, 1.0, 0.0, 1.0, 2.0])  # meridian arcs and the pole
+    np.testing.assert_allclose(got, want, rtol=1e-13, atol=1e-9)
+    np.testing.assert_allclose(oracle_mod.gcd(b, a, R_EARTH), got, rtol=0, atol=0)
+
+
+def test_gcd_matches_chord_of_unit_vectors(oracle_mod):
+    # d = 2 r asin(|u - v| / 2): an independent formula on numpy unit vectors.
+    g = datagen.rng(41)
+    a = np.stack([g.uniform(-180, 180, 2000), np.degrees(np.arcsin(g.uniform(-1, 1, 2000)))], 1)
+    b = a + g.normal(scale=[5.0, 3.0], size=a.shape)
+    b[:, 1] = np.clip(b[:, 1], -90, 90)
+    ua, ub = datagen.sphere_coords(a, 1.0), datagen.sphere_coords(b, 1.0)
+    want = 2.0 * R_EARTH * np.arcsin(np.linalg.norm(ua - ub, axis=1) / 2.0)
+    np.testing.assert_allclose(oracle_mod.gcd(a, b, R_EARTH), want, rtol=1e-11, atol=1e-9)
+    xyz = oracle_mod.sphere_xyz(a)
+    np.testing.assert_allclose(np.linalg.norm(xyz, axis=1), 1.0, rtol=1e-15)
+    np.testing.assert_allclose(xyz, ua, atol=1e-15)
+
+
+def test_knn_sphere_against_numpy_great_circle(oracle_mod):
+    ll = datagen.sphere_locations(3000, 42)
+    xyz = oracle_mod.sphere_xyz(ll)
+    rows = np.array([1, 5, 17, 200, 999, 2999])
+    got = oracle_mod.knn_rows_sphere(xyz, 12, rows)
+    u = datagen.sphere_coords(ll, 1.0)
+    for r, row in zip(rows, got):
+        d = 2.0 * np.arcsin(np.linalg.norm(u[:r] - u[r], axis=1) / 2.0)  # great-circle angle
+        want = np.lexsort((np.arange(r), d))[:min(r, 12)]
+        assert list(row[:min(r, 12)]) == list(want)
+        assert np.all(row[min(r, 12):] == -1)
+
+
+@pytest.mark.parametrize("family,theta", [(0, (1.0, 150.0, 0.5, 0.0)), (0, (1.3, 80.0, 0.5, 0.02)),
+                                          (1, (1.0, 30.0, 0.8, 0.01))])
+def test_sphere_full_conditioning_equals_dense(oracle_mod, family, theta):
+    # m = n-1 Vecchia = Eq. (1) with great-circle distances; the dense likelihood itself
+    # is checked against scipy with a covariance built from numpy's chord formula.
+    n = 80
+    ll = datagen.sphere_locations(n, 43)
+    u = datagen.sphere_coords(ll, 1.0)
+    d = 2.0 * R_EARTH * np.arcsin(np.clip(np.linalg.norm(u[:, None] - u[None], axis=-1) / 2.0, 0, 1))
+    s2, b, nu, t2 = theta
+    if family == 0:
+        C = oracle_mod.matern(d.ravel(), s2, b, nu).reshape(n, n)
+    else:
+        C = s2 * np.exp(-d ** nu / b)
+    S = C + t2 * np.eye(n) + (0.0 if t2 > 0 else 1e-10) * np.eye(n)
+    y = np.linalg.cholesky(S) @ datagen.rng(44).standard_normal(n)
+    ex, gex = oracle_mod.loglik_exact(ll, y, theta, want_grad=True, family=family, radius=R_EARTH)
+    if t2 > 0:
+        want = multivariate_normal(mean=np.zeros(n), cov=C + t2 * np.eye(n)).logpdf(y)
+        assert _rel(ex, want) < 1e-9
+    perm = oracle_mod.order_random(n, 6)
+    va = oracle_mod.vecchia(ll[perm], y[perm], n - 1, theta, want_grad=True, family=family, radius=R_EARTH)
+    assert _rel(va[0], ex) < 1e-10
+    np.testing.assert_allclose(va[1:], gex, rtol=1e-8, atol=1e-8 * np.abs(gex).max())
+
