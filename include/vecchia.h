@@ -98,6 +98,30 @@ int vecchia_plan_create(const double* xy_host, int64_t n, int32_t m, int order, 
 void vecchia_plan_destroy(vecchia_plan_t plan);
 
 /*
+ * vecchia_plan_create_sphere — a plan for (longitude, latitude) data with great-circle
+ * distances (Sec. VI-C, the haversine distance of the paper's real-data study) on a
+ * sphere of radius `radius` (the unit of distance, hence of beta: e.g. 6371 for km).
+ *   lonlat_host : n x 2 doubles (longitude, latitude) in degrees, host memory, copied;
+ *                 |latitude| <= 90.
+ *   order       : VECCHIA_ORDER_GIVEN (perm_in) or VECCHIA_ORDER_RANDOM (seed); the
+ *                 planar orderings (maxmin, Morton) return VECCHIA_EINVAL.
+ *   Conditioning sets: the m_i nearest previously ordered points by great-circle
+ *   distance, found as the smallest (squared chord of the unit vectors, index), the
+ *   squared chord evaluated as ((dx*dx + dy*dy) + dz*dz) in FP64 without fused
+ *   multiply-adds on unit vectors (cos(lat) cos(lon), cos(lat) sin(lon), sin(lat))
+ *   computed on the host from lat, lon times (3.14159265358979323846 / 180).
+ *   The search is a brute-force GPU scan (O(n^2 / 2) candidate checks).
+ * The likelihood calls (vecchia_loglik, _grad, _terms, _autotune) accept the plan;
+ * the batched and allocation-free calls return VECCHIA_EINVAL for it.  Matérn with
+ * great-circle distance is positive definite on the whole sphere only for nu <= 1/2
+ * (and the power exponential for exponent <= 1); larger values may meet
+ * VECCHIA_ENOTPD on global data.  Errors as vecchia_plan_create, plus EINVAL for a
+ * latitude outside [-90, 90] or a radius that is not positive and finite.
+ */
+int vecchia_plan_create_sphere(const double* lonlat_host, int64_t n, int32_t m, int order, uint64_t seed,
+                               const int64_t* perm_in, double radius, void* stream, vecchia_plan_t* out);
+
+/*
  * vecchia_plan_set_kernel — the covariance family used by this plan's likelihood calls:
  * VECCHIA_KERNEL_MATERN (default, Eq. (2)) or VECCHIA_KERNEL_POWEXP (the power
  * exponential of Eq. (3), used by the paper for its real data, Sec. VI-C).  With the

@@ -382,7 +382,8 @@ extern "C" int vecchia_loglik_batched(const vecchia_plan_t* plans, const double*
   using namespace vecchia;
   if (!plans || !y_devs || nfields < 1 || ntheta < 1 || !thetas_dev || !out_dev) return VECCHIA_EINVAL;
   for (int f = 0; f < nfields; ++f)
-    if (!plans[f] || !y_devs[f] || plans[f]->family != kFamilyMatern || plans[f]->m > kMaxMWarp)
+    if (!plans[f] || !y_devs[f] || plans[f]->family != kFamilyMatern || plans[f]->m > kMaxMWarp ||
+        plans[f]->metric != 0)
       return VECCHIA_EINVAL;
   want_grad = want_grad ? 1 : 0;
   int dev = 0;

@@ -34,6 +34,9 @@ struct BigArgs {
   double* partial;  // [gridDim.x][4]
   double* terms;
   unsigned long long* errloc;
+  const double* __restrict__ xyz;  // n x 3 unit vectors (sphere plans)
+  int metric;                      // 0 plane, 1 sphere
+  double radius;
 };
 
 // Largest w with w(w+1)/2 <= e (e < 2^24).
@@ -61,9 +64,11 @@ __global__ void __launch_bounds__(kCtaThreadsMax) vecchia_big_kernel(const BigAr
   const int m = a.m, K = m + 1;
   const int NTd = (K + 1) * (K + 2) / 2, NP = K * (K - 1) / 2;
   double* A = reinterpret_cast<double*>(smem);
+  const bool sphere = a.metric == 1;
   float2* CX = reinterpret_cast<float2*>(A + align_up(NTd, 2));
   float2* CY = CX + align_up(K + 1, 2);
-  double* YV = reinterpret_cast<double*>(CY + align_up(K + 1, 2));
+  float2* CZ = sphere ? CY + align_up(K + 1, 2) : CY;
+  double* YV = reinterpret_cast<double*>(CY + (sphere ? 2 : 1) * align_up(K + 1, 2));
   double* TV = YV + align_up(K + 1, 2);
   double* WH = TV + align_up(K + 1, 2);
   double* GV = WH + align_up(K + 1, 2);
@@ -76,6 +81,14 @@ __global__ void __launch_bounds__(kCtaThreadsMax) vecchia_big_kernel(const BigAr
   ThetaConst tc;
   tc.set(a.sigma2, a.beta, a.tau2, a.family, a.nu);
   const double2* __restrict__ xy2 = reinterpret_cast<const double2*>(a.xy);
+  FieldView F;  // the distance fields pair_u reads
+  F.sphere = sphere;
+  F.xyz = a.xyz;
+  if (sphere) {
+    const double k = 2.0 * a.radius * tc.inv_len;
+    F.k2d = k * k;
+    F.k2 = d2f_pair(F.k2d);
+  }
   Accum acc;
   for (int64_t i = blockIdx.x; i < a.n; i += gridDim.x) {
     const int mi = i < m ? (int)i : m;
@@ -88,22 +101,30 @@ __global__ void __launch_bounds__(kCtaThreadsMax) vecchia_big_kernel(const BigAr
     for (int s = 0; s < 2; ++s) {
       const int p = tid + NTH * s;
       if (p < m) {
-        double xv = 0.0, yv = 0.0, fv = 0.0;
+        double xv = 0.0, yv = 0.0, zv = 0.0, fv = 0.0;
         if (p < mi) {
           const int j = row[p];
-          const double2 q = xy2[j];
-          xv = (q.x - ps.x) * tc.inv_len;
-          yv = (q.y - ps.y) * tc.inv_len;
+          if (sphere) {
+            xv = a.xyz[3 * j] - a.xyz[3 * js];
+            yv = a.xyz[3 * j + 1] - a.xyz[3 * js + 1];
+            zv = a.xyz[3 * j + 2] - a.xyz[3 * js + 2];
+          } else {
+            const double2 q = xy2[j];
+            xv = (q.x - ps.x) * tc.inv_len;
+            yv = (q.y - ps.y) * tc.inv_len;
+          }
           fv = a.yf[j];
         }
         YV[p] = fv;
         CX[p] = d2f_pair(xv);
         CY[p] = d2f_pair(yv);
+        if (sphere) CZ[p] = d2f_pair(zv);
       }
     }
     if (tid == 0) {
       CX[m] = make_float2(0.0f, 0.0f);
       CY[m] = make_float2(0.0f, 0.0f);
+      CZ[m] = make_float2(0.0f, 0.0f);
       YV[m] = a.yf[js];
     }
     __syncthreads();
@@ -124,8 +145,8 @@ __global__ void __launch_bounds__(kCtaThreadsMax) vecchia_big_kernel(const BigAr
       const bool ok0 = c0 < mi && (r0 < mi || r0 == m);
       const bool ok1 = has1 && c1 < mi && (r1 < mi || r1 == m);
       float u0h, u0l, u1h, u1l;
-      sq_dist_df(CX[r0], CX[c0], CY[r0], CY[c0], u0h, u0l);
-      sq_dist_df(CX[r1], CX[c1], CY[r1], CY[c1], u1h, u1l);
+      pair_u(F, CX, CY, CZ, r0, c0, u0h, u0l);
+      pair_u(F, CX, CY, CZ, r1, c1, u1h, u1l);
       const double val0 = rho_df(u0h, u0l, a.tab, mc), val1 = rho_df(u1h, u1l, a.tab, mc);
       A[tri_off(K, c0) + r0 - c0] = ok0 ? val0 : 0.0;
       if (has1) A[tri_off(K, c1) + r1 - c1] = ok1 ? val1 : 0.0;
@@ -253,7 +274,7 @@ __global__ void __launch_bounds__(kCtaThreadsMax) vecchia_big_kernel(const BigAr
         const int v0 = tri_root(q0);
         const int c0 = K - 2 - v0, r0 = c0 + 1 + (q0 - v0 * (v0 + 1) / 2);
         float uh, ul, hh, hl;
-        sq_dist_df(CX[r0], CX[c0], CY[r0], CY[c0], uh, ul);
+        pair_u(F, CX, CY, CZ, r0, c0, uh, ul);
         h_df(uh, ul, a.tab, mc, hh, hl);
         beta_pair_add(WHf[r0], WHf[c0], GVf[r0], GVf[c0], hh, hl, pbh, pbl);
       }
@@ -291,20 +312,20 @@ __global__ void __launch_bounds__(kCtaThreadsMax) vecchia_big_kernel(const BigAr
 }
 
 // Shared memory of the CTA kernel for block size K.
-int big_smem_bytes(int K) {
+int big_smem_bytes(int K, bool sphere) {
   const int NTd = (K + 1) * (K + 2) / 2;
-  return 8 * (align_up(NTd, 2) + 6 * align_up(K + 1, 2) + 32 + 16);
+  return 8 * (align_up(NTd, 2) + (sphere ? 7 : 6) * align_up(K + 1, 2) + 32 + 16);
 }
 
 // CTA size: 128 threads while at least 4 CTAs fit on an SM (more locations in flight),
 // else 256 so that the SM still holds 512 threads.  Measured on GB300 at n = 100k:
 // m = 90 (6 CTAs/SM) 128 threads 1.35x faster than 256; m = 150 (2 CTAs/SM) 256
 // threads 1.34x faster than 128.  VECCHIA_CTA_THREADS = 128 or 256 forces one.
-int big_config(int K, bool grad, int* blocks, int* threads, int* smem) {
+int big_config(int K, bool grad, int* blocks, int* threads, int* smem, bool sphere) {
   int dev = 0, sms = 0;
   VECCHIA_CUDA_TRY(cudaGetDevice(&dev));
   VECCHIA_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  *smem = big_smem_bytes(K);
+  *smem = big_smem_bytes(K, sphere);
   auto kern = grad ? vecchia_big_kernel<true> : vecchia_big_kernel<false>;
   VECCHIA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, *smem));
   const char* e = getenv("VECCHIA_CTA_THREADS");

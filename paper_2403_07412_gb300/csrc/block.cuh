@@ -57,19 +57,21 @@ struct SchedSize {
 // block rows' coordinates CX, CY (float pairs), the data YV (assembly only) and the
 // pivot column TV (elimination only).  The adjoint's weight vectors WH and GV reuse
 // YV and TV, so the gradient kernel fits as many warps per SM as the forward one.
+// On the sphere a third coordinate array CZ follows CY.
 struct WarpArea {
   double *A, *YV, *TV, *WH, *GV;
-  float2 *CX, *CY;
-  __host__ __device__ static int doubles(int K, bool /*grad*/) {
+  float2 *CX, *CY, *CZ;
+  __host__ __device__ static int doubles(int K, bool /*grad*/, bool sphere = false) {
     const SchedSize S(K);
-    return align_up(S.NT, 2) + 4 * align_up(K + 1, 2);
+    return align_up(S.NT, 2) + (sphere ? 5 : 4) * align_up(K + 1, 2);
   }
-  __device__ WarpArea(double* base, int K) {
+  __device__ WarpArea(double* base, int K, bool sphere = false) {
     const SchedSize S(K);
     A = base;
     CX = reinterpret_cast<float2*>(A + align_up(S.NT, 2));
     CY = CX + align_up(K + 1, 2);
-    YV = reinterpret_cast<double*>(CY + align_up(K + 1, 2));
+    CZ = sphere ? CY + align_up(K + 1, 2) : CY;
+    YV = reinterpret_cast<double*>(CY + (sphere ? 2 : 1) * align_up(K + 1, 2));
     TV = YV + align_up(K + 1, 2);
     WH = YV;
     GV = TV;
@@ -137,6 +139,12 @@ struct FieldView {
   const int32_t* __restrict__ self; // n
   int64_t n;
   int m;
+  // great-circle distances: unit vectors (n x 3, original order) and K2 = (2 r / len)^2,
+  // with len the family's length scale, as a float pair and in FP64
+  const double* __restrict__ xyz = nullptr;
+  bool sphere = false;
+  float2 k2 = make_float2(0.0f, 0.0f);
+  double k2d = 0.0;
 };
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -204,6 +212,74 @@ __device__ __forceinline__ void sq_dist_df(float2 xr, float2 xc, float2 yr, floa
   ul = __fsub_rn(e, __fsub_rn(uh, s));
 }
 
+// Squared chord between two points on the unit sphere held as float-pair offsets, in
+// double-float arithmetic (as sq_dist_df, with three coordinates).
+__device__ __forceinline__ void sq_chord_df(float2 xr, float2 xc, float2 yr, float2 yc, float2 zr, float2 zc,
+                                            float& ch, float& cl) {
+  float dxh, dxl, dyh, dyl, dzh, dzl;
+  df_diff(xr, xc, dxh, dxl);
+  df_diff(yr, yc, dyh, dyl);
+  df_diff(zr, zc, dzh, dzl);
+  const float px = __fmul_rn(dxh, dxh), py = __fmul_rn(dyh, dyh), pz = __fmul_rn(dzh, dzh);
+  float ex = fmaf(dxh, dxh, -px), ey = fmaf(dyh, dyh, -py), ez = fmaf(dzh, dzh, -pz);
+  ex = fmaf(dxh + dxh, dxl, ex);
+  ey = fmaf(dyh + dyh, dyl, ey);
+  ez = fmaf(dzh + dzh, dzl, ez);
+  float s1, e1, s2, e2;
+  two_sum(px, py, s1, e1);
+  two_sum(s1, pz, s2, e2);
+  float e = __fadd_rn(__fadd_rn(e1, e2), __fadd_rn(__fadd_rn(ex, ey), ez));
+  ch = __fadd_rn(s2, e);
+  cl = __fsub_rn(e, __fsub_rn(ch, s2));
+}
+
+// u = K2 asin^2(c / 2) from the squared chord c^2 = ch + cl of two unit vectors: the
+// great-circle distance d = 2 r asin(c / 2) (Sec. VI-C), over the length scale, squared.
+// With w = c^2 / 4, asin^2(sqrt(w)) = w + w^2 T(w), T(w) = 1/3 + 8w/45 + 4w^2/35 +
+// 128w^3/1575 + 128w^4/2079 (the series sum_k 2^(2k-1) w^k / (k^2 C(2k,k))), whose
+// next term is below 2^-50 w for w <= 2^-10, i.e. chords up to 1/16 of the radius;
+// longer chords take FP64 asin.  Double-float arithmetic otherwise, as sq_dist_df.
+__device__ __forceinline__ void sphere_u_df(float ch, float cl, const FieldView& F, float& uh, float& ul) {
+  const float wh = ch * 0.25f, wl = cl * 0.25f;
+  if (wh > 0x1p-10f) {
+    const double a = asin(sqrt(f2d_scaled(wh, 0) + f2d_scaled(wl, 0)));
+    const float2 u = d2f_pair(F.k2d * a * a);
+    uh = u.x;
+    ul = u.y;
+    return;
+  }
+  constexpr float kThirdH = 1.0f / 3.0f;
+  constexpr float kThirdL = (float)(1.0 / 3.0 - (double)(1.0f / 3.0f));
+  constexpr float k845H = 8.0f / 45.0f;
+  constexpr float k845L = (float)(8.0 / 45.0 - (double)(8.0f / 45.0f));
+  const float r = fmaf(fmaf(128.0f / 2079.0f, wh, 128.0f / 1575.0f), wh, 4.0f / 35.0f);
+  float t1h, t1l, s, e;
+  df_mul(wh, wl, k845H, k845L, t1h, t1l);
+  two_sum(kThirdH, t1h, s, e);
+  e = __fadd_rn(e, __fadd_rn(__fadd_rn(t1l, kThirdL), __fmul_rn(__fmul_rn(wh, wh), r)));
+  const float th = __fadd_rn(s, e), tl = __fsub_rn(e, __fsub_rn(th, s));
+  float ah, al, bh, bl;
+  df_mul(wh, wl, th, tl, ah, al);  // w T
+  df_mul(wh, wl, ah, al, bh, bl);  // w^2 T
+  two_sum(wh, bh, s, e);
+  e = __fadd_rn(e, __fadd_rn(wl, bl));
+  const float vh = __fadd_rn(s, e), vl = __fsub_rn(e, __fsub_rn(vh, s));
+  df_mul(F.k2.x, F.k2.y, vh, vl, uh, ul);
+}
+
+// u of the pair (r, c) of the block, plane or sphere.
+__device__ __forceinline__ void pair_u(const FieldView& F, const float2* __restrict__ CX,
+                                       const float2* __restrict__ CY, const float2* __restrict__ CZ, int r, int c,
+                                       float& uh, float& ul) {
+  if (F.sphere) {
+    float ch, cl;
+    sq_chord_df(CX[r], CX[c], CY[r], CY[c], CZ[r], CZ[c], ch, cl);
+    sphere_u_df(ch, cl, F, uh, ul);
+  } else {
+    sq_dist_df(CX[r], CX[c], CY[r], CY[c], uh, ul);
+  }
+}
+
 // (pbh, pbl) += h (w_r g_c + w_c g_r) in double-float arithmetic.
 __device__ __forceinline__ void beta_pair_add(float2 wr, float2 wc, float2 gr, float2 gc, float hh, float hl,
                                               float& pbh, float& pbl) {
@@ -235,6 +311,7 @@ __device__ __forceinline__ void process_location(int64_t i, bool active, const F
   double* __restrict__ A = W.A;
   float2* __restrict__ CX = W.CX;
   float2* __restrict__ CY = W.CY;
+  float2* __restrict__ CZ = W.CZ;
   double* __restrict__ YV = W.YV;
   double* __restrict__ TV = W.TV;
   const int mi = i < m ? (int)i : m;
@@ -246,22 +323,30 @@ __device__ __forceinline__ void process_location(int64_t i, bool active, const F
   for (int s = 0; s < NSG; ++s) {
     const int p = sub + G * s;
     if (p < m) {
-      double xv = 0.0, yv = 0.0, fv = 0.0;
+      double xv = 0.0, yv = 0.0, zv = 0.0, fv = 0.0;
       if (p < mi) {
         const int j = row[p];
-        const double2 q = F.xy[j];
-        xv = (q.x - ps.x) * tc.inv_len;
-        yv = (q.y - ps.y) * tc.inv_len;
+        if (F.sphere) {  // unit-vector offsets; the length scale enters through K2
+          xv = F.xyz[3 * j] - F.xyz[3 * js];
+          yv = F.xyz[3 * j + 1] - F.xyz[3 * js + 1];
+          zv = F.xyz[3 * j + 2] - F.xyz[3 * js + 2];
+        } else {
+          const double2 q = F.xy[j];
+          xv = (q.x - ps.x) * tc.inv_len;
+          yv = (q.y - ps.y) * tc.inv_len;
+        }
         fv = F.yf[j];
       }
       YV[p] = fv;
       CX[p] = d2f_pair(xv);
       CY[p] = d2f_pair(yv);
+      if (F.sphere) CZ[p] = d2f_pair(zv);
     }
   }
   if (sub == 0) {
     CX[m] = make_float2(0.0f, 0.0f);
     CY[m] = make_float2(0.0f, 0.0f);
+    CZ[m] = make_float2(0.0f, 0.0f);
     YV[m] = F.yf[js];
   }
   __syncwarp();
@@ -283,8 +368,8 @@ __device__ __forceinline__ void process_location(int64_t i, bool active, const F
     const bool v0 = c0 < mi && (r0 < mi || r0 == m);
     const bool v1 = has1 && c1 < mi && (r1 < mi || r1 == m);
     float u0h, u0l, u1h, u1l;
-    sq_dist_df(CX[r0], CX[c0], CY[r0], CY[c0], u0h, u0l);
-    sq_dist_df(CX[r1], CX[c1], CY[r1], CY[c1], u1h, u1l);
+    pair_u(F, CX, CY, CZ, r0, c0, u0h, u0l);
+    pair_u(F, CX, CY, CZ, r1, c1, u1h, u1l);
     const double val0 = rho_df(u0h, u0l, tab, mc), val1 = rho_df(u1h, u1l, tab, mc);
     A[w0 >> 16] = v0 ? val0 : 0.0;
     if (has1) A[w1 >> 16] = v1 ? val1 : 0.0;
@@ -442,8 +527,8 @@ __device__ __forceinline__ void process_location(int64_t i, bool active, const F
     const int r0 = w0 & 0xFF, c0 = (w0 >> 8) & 0xFF;
     const int r1 = w1 & 0xFF, c1 = (w1 >> 8) & 0xFF;
     float u0h, u0l, u1h, u1l;
-    sq_dist_df(CX[r0], CX[c0], CY[r0], CY[c0], u0h, u0l);
-    sq_dist_df(CX[r1], CX[c1], CY[r1], CY[c1], u1h, u1l);
+    pair_u(F, CX, CY, CZ, r0, c0, u0h, u0l);
+    pair_u(F, CX, CY, CZ, r1, c1, u1h, u1l);
     float h0h, h0l, h1h, h1l;
     h_df(u0h, u0l, tab, mc, h0h, h0l);
     h_df(u1h, u1l, tab, mc, h1h, h1l);

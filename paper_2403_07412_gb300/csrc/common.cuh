@@ -38,7 +38,10 @@ struct Plan {
   int32_t m = 0;
   int family = kFamilyMatern;
   int device = 0;
-  double* d_xy = nullptr;     // n x 2, original order
+  int metric = 0;             // 0: plane (Euclidean), 1: sphere (great-circle distance)
+  double radius = 1.0;        // sphere radius (metric 1)
+  double* d_xy = nullptr;     // n x 2, original order (longitude, latitude for metric 1)
+  double* d_xyz = nullptr;    // n x 3 unit vectors, original order (metric 1)
   int32_t* d_nbr = nullptr;   // n x m, ORIGINAL indices of J_i, -1 padded (ordered rows)
   int32_t* d_self = nullptr;  // n, original index of ordered location i
   int64_t* h_perm = nullptr;  // n, host copy of the ordering

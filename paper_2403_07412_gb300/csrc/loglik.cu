@@ -33,8 +33,11 @@ struct BigArgs {
   double* partial;
   double* terms;
   unsigned long long* errloc;
+  const double* __restrict__ xyz;  // n x 3 unit vectors (sphere plans)
+  int metric;                      // 0 plane, 1 sphere
+  double radius;
 };
-int big_config(int K, bool grad, int* blocks, int* threads, int* smem);
+int big_config(int K, bool grad, int* blocks, int* threads, int* smem, bool sphere);
 void launch_big(bool grad, int blocks, int threads, int smem, const BigArgs& a, cudaStream_t s);
 bool theta_ok_family(const double* th, int family);
 int launch_matern_table(double nu, double* tab, cudaStream_t stream);
@@ -53,6 +56,9 @@ struct LikArgs {
   double* partial;                   // [nwarps][4]
   double* terms;                     // optional [n][1|4]
   unsigned long long* errloc;
+  const double* __restrict__ xyz = nullptr;  // n x 3 unit vectors (sphere plans)
+  int metric = 0;                    // 0 plane, 1 sphere
+  double radius = 1.0;
 };
 
 // Shared-memory layout for block size K (= m + 1), G lanes per location (32/G locations
@@ -60,8 +66,10 @@ struct LikArgs {
 struct SmemLayout {
   SchedSize S;
   int group_doubles, per_warp_doubles;
-  __host__ __device__ SmemLayout(int K, bool grad, int G)
-      : S(K), group_doubles(WarpArea::doubles(K, grad)), per_warp_doubles((32 / G) * WarpArea::doubles(K, grad)) {}
+  __host__ __device__ SmemLayout(int K, bool grad, int G, bool sphere = false)
+      : S(K),
+        group_doubles(WarpArea::doubles(K, grad, sphere)),
+        per_warp_doubles((32 / G) * WarpArea::doubles(K, grad, sphere)) {}
   __host__ __device__ int bytes(int W) const { return S.sched_bytes + S.pairs_bytes + W * per_warp_doubles * 8; }
 };
 
@@ -70,7 +78,8 @@ __global__ void __launch_bounds__(384) vecchia_lik_kernel(const LikArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int NL = 32 / G;
   const int K = a.m + 1;
-  const SmemLayout L(K, GRAD, G);
+  const bool sphere = a.metric == 1;
+  const SmemLayout L(K, GRAD, G, sphere);
   uint16_t* sched = reinterpret_cast<uint16_t*>(smem);
   uint32_t* pairs = reinterpret_cast<uint32_t*>(smem + L.S.sched_bytes);
   const int lane = threadIdx.x & 31;
@@ -78,7 +87,7 @@ __global__ void __launch_bounds__(384) vecchia_lik_kernel(const LikArgs a) {
   const int W = blockDim.x >> 5;
   const int grp = lane / G, sub = lane % G;
   const WarpArea area(reinterpret_cast<double*>(smem + L.S.sched_bytes + L.S.pairs_bytes) +
-                          wib * L.per_warp_doubles + grp * L.group_doubles, K);
+                          wib * L.per_warp_doubles + grp * L.group_doubles, K, sphere);
   build_schedules(K, sched, pairs);
   __syncthreads();
 
@@ -92,6 +101,13 @@ __global__ void __launch_bounds__(384) vecchia_lik_kernel(const LikArgs a) {
   F.self = a.self;
   F.n = a.n;
   F.m = a.m;
+  if (sphere) {
+    F.sphere = true;
+    F.xyz = a.xyz;
+    const double k = 2.0 * a.radius * tc.inv_len;
+    F.k2d = k * k;
+    F.k2 = d2f_pair(F.k2d);
+  }
   const int64_t gw = (int64_t)blockIdx.x * W + wib;
   const int64_t nw = (int64_t)gridDim.x * W;
   const bool terms_mode = a.terms != nullptr;
@@ -180,12 +196,12 @@ void set_tuned(int dev, int K, bool grad, int G, int W) {
 
 // Launch shape for lanes-per-location G: W (forced_W > 0, else the value giving the most
 // resident warps per SM, ties to the larger CTA) and a persistent grid of one wave.
-int shape_for(int K, bool grad, int G, int forced_W, LaunchCfg* cfg) {
+int shape_for(int K, bool grad, int G, int forced_W, LaunchCfg* cfg, bool sphere = false) {
   int dev = 0, sms = 0, smem_optin = 0;
   VECCHIA_CUDA_TRY(cudaGetDevice(&dev));
   VECCHIA_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   VECCHIA_CUDA_TRY(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  const SmemLayout L(K, grad, G);
+  const SmemLayout L(K, grad, G, sphere);
   void* kern = lik_kernel(grad, G);
   int best_warps = -1;
   for (int W : {12, 11, 10, 9, 8, 6, 4, 2, 1}) {
@@ -212,17 +228,18 @@ int shape_for(int K, bool grad, int G, int forced_W, LaunchCfg* cfg) {
 // Configuration for block size K: the tuned shape if vecchia_autotune recorded one, else
 // the default lanes per location.  VECCHIA_LANES_PER_LOCATION / VECCHIA_WARPS_PER_CTA
 // force either value (tuning experiments).
-int pick_config(int K, bool grad, LaunchCfg* cfg) {
+int pick_config(int K, bool grad, LaunchCfg* cfg, bool sphere = false) {
   int dev = 0;
   VECCHIA_CUDA_TRY(cudaGetDevice(&dev));
   int G = default_lanes(K), W = 0;
   tuned_for(dev, K, grad, &G, &W);
+  if (sphere) W = 0;  // the tuned CTA size was sized for planar blocks
   if (const char* e = getenv("VECCHIA_LANES_PER_LOCATION")) {
     const int v = atoi(e);
     if (v == 8 || v == 16 || v == 32) G = v;
   }
   if (const char* e = getenv("VECCHIA_WARPS_PER_CTA")) W = atoi(e);
-  return shape_for(K, grad, G, W, cfg);
+  return shape_for(K, grad, G, W, cfg, sphere);
 }
 
 void launch_lik(const LaunchCfg& cfg, bool grad, const LikArgs& a, cudaStream_t stream) {
@@ -278,6 +295,9 @@ int launch_with(Plan* p, const double* y_dev, const double* theta, bool grad, co
   a.partial = p->d_partial;
   a.terms = terms_dev;
   a.errloc = p->d_errloc;
+  a.xyz = p->d_xyz;
+  a.metric = p->metric;
+  a.radius = p->radius;
   launch_lik(cfg, grad, a, stream);
   VECCHIA_CUDA_TRY(cudaGetLastError());
   if (out_dev) {
@@ -295,7 +315,7 @@ int launch_with(Plan* p, const double* y_dev, const double* theta, bool grad, co
 static int launch_big_loglik(Plan* p, const double* y_dev, const double* theta, bool grad, double* out_dev,
                              double* terms_dev, cudaStream_t stream) {
   int blocks = 0, threads = 0, smem = 0;
-  int rc = big_config(p->m + 1, grad, &blocks, &threads, &smem);
+  int rc = big_config(p->m + 1, grad, &blocks, &threads, &smem, p->metric == 1);
   if (rc) return rc;
   if (p->partial_cap < (int64_t)blocks * 4) {
     if (p->d_partial) cudaFree(p->d_partial);
@@ -324,6 +344,9 @@ static int launch_big_loglik(Plan* p, const double* y_dev, const double* theta, 
   a.partial = p->d_partial;
   a.terms = terms_dev;
   a.errloc = p->d_errloc;
+  a.xyz = p->d_xyz;
+  a.metric = p->metric;
+  a.radius = p->radius;
   launch_big(grad, blocks, threads, smem, a, stream);
   VECCHIA_CUDA_TRY(cudaGetLastError());
   if (out_dev) {
@@ -341,7 +364,7 @@ int launch_loglik(Plan* p, const double* y_dev, const double* theta, bool grad, 
   if (!p || !y_dev || !theta_ok_family(theta, p->family) || (!out_dev && !terms_dev)) return VECCHIA_EINVAL;
   if (p->m > kMaxMWarp) return launch_big_loglik(p, y_dev, theta, grad, out_dev, terms_dev, stream);
   LaunchCfg cfg;
-  int rc = pick_config(p->m + 1, grad, &cfg);
+  int rc = pick_config(p->m + 1, grad, &cfg, p->metric == 1);
   if (rc) return rc;
   return launch_with(p, y_dev, theta, grad, cfg, out_dev, terms_dev, stream);
 }
@@ -369,7 +392,7 @@ int autotune(Plan* p, const double* y_dev, const double* theta, bool grad, int* 
   for (int G : {8, 16, 32}) {
     for (int W : {12, 11, 10, 9, 8, 6, 4}) {
       LaunchCfg cfg;
-      if (shape_for(K, grad, G, W, &cfg) != VECCHIA_OK) continue;
+      if (shape_for(K, grad, G, W, &cfg, p->metric == 1) != VECCHIA_OK) continue;
       float tmin = 1e30f;
       for (int rep = 0; rep < 3 && !rc; ++rep) {
         cudaEventRecord(e0, stream);

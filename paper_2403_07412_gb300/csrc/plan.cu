@@ -396,8 +396,125 @@ static int knn_gpu(Plan* p, const double* xy_host, cudaStream_t stream) {
   return rc;
 }
 
+// ------------------------------------------------------------------ sphere
+// Unit vectors of (longitude, latitude) points in degrees, on the host.
+static void sphere_unit_vectors(int64_t n, const double* lonlat, double* xyz) {
+  const double rad = 3.14159265358979323846 / 180.0;
+  for (int64_t i = 0; i < n; ++i) {
+    const double lam = lonlat[2 * i] * rad, phi = lonlat[2 * i + 1] * rad;
+    const double cp = cos(phi);
+    xyz[3 * i] = cp * cos(lam);
+    xyz[3 * i + 1] = cp * sin(lam);
+    xyz[3 * i + 2] = sin(phi);
+  }
+}
+
+struct SphereKnnArgs {
+  const double* __restrict__ xyzo;  // ordered unit vectors, n x 3
+  int64_t n;
+  int m;
+  const int64_t* __restrict__ perm;  // ordered -> original
+  int32_t* nbr;                      // n x m, ORIGINAL indices
+};
+
+constexpr int kSphereTile = 256;
+
+// Brute-force search on the sphere: one thread per ordered query i scans every j < i,
+// with CTA-wide tiles of candidates staged in shared memory.  Candidates whose FP32
+// squared chord exceeds the current m-th best by more than its rounding bound are
+// skipped; the rest are ranked by the exact FP64 key ((dx*dx + dy*dy) + dz*dz, no
+// fused operations) and the index.
+__global__ void __launch_bounds__(128) knn_sphere_kernel(const SphereKnnArgs a) {
+  __shared__ double tx[kSphereTile], ty[kSphereTile], tz[kSphereTile];
+  __shared__ float fx[kSphereTile], fy[kSphereTile], fz[kSphereTile];
+  const int64_t i0 = (int64_t)blockIdx.x * blockDim.x;
+  const int64_t i = i0 + threadIdx.x;
+  const bool live = i < a.n;
+  const int m = a.m;
+  const int mi = live ? (int)(i < m ? i : m) : 0;
+  BestList bl;
+  bl.cnt = 0;
+  double qx = 0.0, qy = 0.0, qz = 0.0;
+  if (live) {
+    qx = a.xyzo[3 * i];
+    qy = a.xyzo[3 * i + 1];
+    qz = a.xyzo[3 * i + 2];
+  }
+  const float gx = (float)qx, gy = (float)qy, gz = (float)qz;
+  float wf = INFINITY;  // prefilter threshold (stays infinite until the list is full)
+  const int64_t jend = min(a.n, i0 + (int64_t)blockDim.x) - 1;  // largest i in the block, exclusive bound
+  for (int64_t t0 = 0; t0 < jend; t0 += kSphereTile) {
+    __syncthreads();
+    for (int k = threadIdx.x; k < kSphereTile; k += blockDim.x) {
+      const int64_t j = t0 + k;
+      if (j < a.n) {
+        const double x = a.xyzo[3 * j], y = a.xyzo[3 * j + 1], z = a.xyzo[3 * j + 2];
+        tx[k] = x;
+        ty[k] = y;
+        tz[k] = z;
+        fx[k] = (float)x;
+        fy[k] = (float)y;
+        fz[k] = (float)z;
+      }
+    }
+    __syncthreads();
+    if (!live) continue;
+    const int kend = (int)min((int64_t)kSphereTile, i - t0);
+    for (int k = 0; k < kend; ++k) {
+      const float ex = fx[k] - gx, ey = fy[k] - gy, ez = fz[k] - gz;
+      if (ex * ex + ey * ey + ez * ez > wf) continue;
+      const double dx = __dsub_rn(tx[k], qx), dy = __dsub_rn(ty[k], qy), dz = __dsub_rn(tz[k], qz);
+      const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+      const int cnt0 = bl.cnt;
+      const long long worst0 = cnt0 == mi && mi > 0 ? bl.d[mi - 1] : -1;
+      bl.offer(__double_as_longlong(d2), (int)(t0 + k), mi);
+      if (bl.cnt == mi && mi > 0 && (cnt0 != mi || bl.d[mi - 1] != worst0)) {
+        // FP32 chord^2 differs from the exact one by at most 6 * 2^-24 sqrt(3) |chord|
+        // + 3 * 2^-24 chord^2 + 27 * 2^-48 (unit vectors): skip only beyond that.
+        const double w = __longlong_as_double(bl.d[mi - 1]);
+        wf = __double2float_ru(w + 1.2e-6 * sqrt(w) + 2.5e-7 * w + 3e-13);
+      }
+    }
+  }
+  if (!live) return;
+  int32_t* out = a.nbr + i * m;
+  for (int p = 0; p < m; ++p) out[p] = p < bl.cnt ? (int32_t)a.perm[bl.id[p]] : -1;
+}
+
+static int knn_sphere_gpu(Plan* p, const double* xyz_host, cudaStream_t stream) {
+  const int64_t n = p->n;
+  std::vector<double> xyzo(3 * n);
+  for (int64_t k = 0; k < n; ++k)
+    for (int c = 0; c < 3; ++c) xyzo[3 * k + c] = xyz_host[3 * p->h_perm[k] + c];
+  double* d_xyzo = nullptr;
+  int64_t* d_perm = nullptr;
+  int rc = VECCHIA_OK;
+  if (cudaMalloc(&d_xyzo, sizeof(double) * 3 * n) != cudaSuccess ||
+      cudaMalloc(&d_perm, sizeof(int64_t) * n) != cudaSuccess)
+    rc = VECCHIA_ENOMEM;
+  if (!rc && (cudaMemcpyAsync(d_xyzo, xyzo.data(), sizeof(double) * 3 * n, cudaMemcpyHostToDevice, stream) !=
+                  cudaSuccess ||
+              cudaMemcpyAsync(d_perm, p->h_perm, sizeof(int64_t) * n, cudaMemcpyHostToDevice, stream) != cudaSuccess))
+    rc = VECCHIA_ECUDA;
+  if (!rc) {
+    SphereKnnArgs a;
+    a.xyzo = d_xyzo;
+    a.n = n;
+    a.m = p->m;
+    a.perm = d_perm;
+    a.nbr = p->d_nbr;
+    knn_sphere_kernel<<<(unsigned)((n + 127) / 128), 128, 0, stream>>>(a);
+    if (cudaGetLastError() != cudaSuccess) rc = VECCHIA_ECUDA;
+  }
+  if (!rc && cudaStreamSynchronize(stream) != cudaSuccess) rc = VECCHIA_ECUDA;
+  cudaFree(d_xyzo);
+  cudaFree(d_perm);
+  return rc;
+}
+
 static void plan_free(Plan* p) {
   if (!p) return;
+  cudaFree(p->d_xyz);
   cudaFree(p->d_xy);
   cudaFree(p->d_nbr);
   cudaFree(p->d_self);
@@ -414,15 +531,9 @@ void forget_plan_in_batches(const void* plan);
 int autotune(Plan* p, const double* y_dev, const double* theta, bool grad, int* G_out, int* W_out,
              cudaStream_t stream);
 
-}  // namespace vecchia
-
-using vecchia::Plan;
-
-extern "C" {
-
-int vecchia_plan_create(const double* xy_host, int64_t n, int32_t m, int order, uint64_t seed,
-                        const int64_t* perm_in, void* stream, vecchia_plan_t* out) {
-  using namespace vecchia;
+// Plan construction for both metrics (metric 0: plane, 1: sphere of the given radius).
+static int plan_create(const double* xy_host, int64_t n, int32_t m, int order, uint64_t seed,
+                       const int64_t* perm_in, int metric, double radius, void* stream, vecchia_plan_t* out) {
   if (!out) return VECCHIA_EINVAL;
   *out = nullptr;
   if (!xy_host || n < 1 || n > 2147483647LL || m < 1 || m > kMaxM) return VECCHIA_EINVAL;
@@ -431,10 +542,18 @@ int vecchia_plan_create(const double* xy_host, int64_t n, int32_t m, int order, 
     return VECCHIA_EINVAL;
   for (int64_t i = 0; i < 2 * n; ++i)
     if (!std::isfinite(xy_host[i])) return VECCHIA_EINVAL;
+  if (metric == 1) {
+    if (!(radius > 0.0) || !std::isfinite(radius)) return VECCHIA_EINVAL;
+    if (order != VECCHIA_ORDER_GIVEN && order != VECCHIA_ORDER_RANDOM) return VECCHIA_EINVAL;
+    for (int64_t i = 0; i < n; ++i)
+      if (!(fabs(xy_host[2 * i + 1]) <= 90.0)) return VECCHIA_EINVAL;
+  }
   vecchia_plan* p = new (std::nothrow) vecchia_plan();
   if (!p) return VECCHIA_ENOMEM;
   p->n = n;
   p->m = m;
+  p->metric = metric;
+  p->radius = radius;
   cudaGetDevice(&p->device);
   p->h_perm = new (std::nothrow) int64_t[n];
   if (!p->h_perm) { plan_free(p); return VECCHIA_ENOMEM; }
@@ -460,7 +579,8 @@ int vecchia_plan_create(const double* xy_host, int64_t n, int32_t m, int order, 
       cudaMalloc(&p->d_nbr, sizeof(int32_t) * n * m) != cudaSuccess ||
       cudaMalloc(&p->d_self, sizeof(int32_t) * n) != cudaSuccess ||
       cudaMalloc(&p->d_inv, sizeof(int32_t) * n) != cudaSuccess ||
-      cudaMalloc(&p->d_errloc, sizeof(unsigned long long)) != cudaSuccess) {
+      cudaMalloc(&p->d_errloc, sizeof(unsigned long long)) != cudaSuccess ||
+      (metric == 1 && cudaMalloc(&p->d_xyz, sizeof(double) * 3 * n) != cudaSuccess)) {
     plan_free(p);
     return VECCHIA_ENOMEM;
   }
@@ -469,18 +589,41 @@ int vecchia_plan_create(const double* xy_host, int64_t n, int32_t m, int order, 
     self[k] = (int32_t)p->h_perm[k];
     inv[p->h_perm[k]] = (int32_t)k;
   }
+  std::vector<double> xyz;
+  if (metric == 1) {
+    xyz.resize(3 * n);
+    sphere_unit_vectors(n, xy_host, xyz.data());
+  }
   if (cudaMemcpyAsync(p->d_xy, xy_host, sizeof(double) * 2 * n, cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaMemcpyAsync(p->d_self, self.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaMemcpyAsync(p->d_inv, inv.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-      cudaMemsetAsync(p->d_errloc, 0xFF, sizeof(unsigned long long), s) != cudaSuccess) {
+      cudaMemsetAsync(p->d_errloc, 0xFF, sizeof(unsigned long long), s) != cudaSuccess ||
+      (metric == 1 && cudaMemcpyAsync(p->d_xyz, xyz.data(), sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s) !=
+                          cudaSuccess)) {
     plan_free(p);
     return VECCHIA_ECUDA;
   }
-  rc = knn_gpu(p, xy_host, s);
+  rc = metric == 1 ? knn_sphere_gpu(p, xyz.data(), s) : knn_gpu(p, xy_host, s);
   if (rc) { plan_free(p); return rc; }
   p->last_stream = s;
   *out = p;
   return VECCHIA_OK;
+}
+
+}  // namespace vecchia
+
+using vecchia::Plan;
+
+extern "C" {
+
+int vecchia_plan_create(const double* xy_host, int64_t n, int32_t m, int order, uint64_t seed,
+                        const int64_t* perm_in, void* stream, vecchia_plan_t* out) {
+  return vecchia::plan_create(xy_host, n, m, order, seed, perm_in, 0, 1.0, stream, out);
+}
+
+int vecchia_plan_create_sphere(const double* lonlat_host, int64_t n, int32_t m, int order, uint64_t seed,
+                               const int64_t* perm_in, double radius, void* stream, vecchia_plan_t* out) {
+  return vecchia::plan_create(lonlat_host, n, m, order, seed, perm_in, 1, radius, stream, out);
 }
 
 void vecchia_plan_destroy(vecchia_plan_t plan) {

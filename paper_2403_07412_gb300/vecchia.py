@@ -41,6 +41,8 @@ _dp = ctypes.POINTER(ctypes.c_double)
 SIGNATURES = {
     "vecchia_plan_create": (ctypes.c_int, [_dp, _i64, _i32, ctypes.c_int, ctypes.c_uint64,
                                            ctypes.POINTER(_i64), _vp, ctypes.POINTER(_vp)]),
+    "vecchia_plan_create_sphere": (ctypes.c_int, [_dp, _i64, _i32, ctypes.c_int, ctypes.c_uint64,
+                                                  ctypes.POINTER(_i64), ctypes.c_double, _vp, ctypes.POINTER(_vp)]),
     "vecchia_plan_destroy": (None, [_vp]),
     "vecchia_plan_size": (ctypes.c_int, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i32)]),
     "vecchia_plan_set_kernel": (ctypes.c_int, [_vp, ctypes.c_int]),
@@ -114,21 +116,32 @@ def _dev_f64(x: torch.Tensor, n: int, name: str) -> torch.Tensor:
 
 
 class Plan:
-    """Ordering and conditioning sets for one set of locations (vecchia_plan_create)."""
+    """Ordering and conditioning sets for one set of locations (vecchia_plan_create).
 
-    def __init__(self, xy, m: int, order: int = ORDER_RANDOM, seed: int = 0, perm=None, stream=None):
+    With ``radius`` given, ``xy`` holds (longitude, latitude) in degrees and distances are
+    great-circle distances on a sphere of that radius (vecchia_plan_create_sphere).
+    """
+
+    def __init__(self, xy, m: int, order: int = ORDER_RANDOM, seed: int = 0, perm=None, stream=None,
+                 radius=None):
         xy = np.ascontiguousarray(np.asarray(xy, dtype=np.float64).reshape(-1, 2))
         self.n = int(xy.shape[0])
         self.m = int(m)
+        self.radius = radius
         h = _vp()
         pin = None
         if order == ORDER_GIVEN:
             pin = np.ascontiguousarray(np.asarray(perm, dtype=np.int64))
-        rc = lib().vecchia_plan_create(xy.ctypes.data_as(_dp), self.n, self.m, int(order),
-                                       ctypes.c_uint64(int(seed) & 0xFFFFFFFFFFFFFFFF),
-                                       pin.ctypes.data_as(ctypes.POINTER(_i64)) if pin is not None else None,
-                                       _vp(_stream(stream)), ctypes.byref(h))
-        _check(rc, "vecchia_plan_create")
+        pin_p = pin.ctypes.data_as(ctypes.POINTER(_i64)) if pin is not None else None
+        seed_c = ctypes.c_uint64(int(seed) & 0xFFFFFFFFFFFFFFFF)
+        if radius is None:
+            rc = lib().vecchia_plan_create(xy.ctypes.data_as(_dp), self.n, self.m, int(order), seed_c, pin_p,
+                                           _vp(_stream(stream)), ctypes.byref(h))
+            _check(rc, "vecchia_plan_create")
+        else:
+            rc = lib().vecchia_plan_create_sphere(xy.ctypes.data_as(_dp), self.n, self.m, int(order), seed_c,
+                                                  pin_p, float(radius), _vp(_stream(stream)), ctypes.byref(h))
+            _check(rc, "vecchia_plan_create_sphere")
         self._h = h
 
     @property

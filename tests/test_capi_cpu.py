@@ -59,3 +59,24 @@ def test_strerror_and_argument_checks_without_gpu(libpath):
     th = (ctypes.c_double * 4)(1.0, -0.1, 0.5, 0.0)
     assert L.vecchia_matern(None, 1, th, None, None, None) == vecchia.EINVAL
     assert L.vecchia_loglik(None, None, th, None, None) == vecchia.EINVAL
+
+
+def test_sphere_plan_argument_checks_without_gpu(libpath):
+    from paper_2403_07412_gb300 import vecchia
+
+    L = vecchia.lib()
+    out = ctypes.c_void_p()
+    ll = (ctypes.c_double * 4)(-90.0, 35.0, -89.0, 36.0)
+    bad_lat = (ctypes.c_double * 4)(-90.0, 95.0, -89.0, 36.0)
+    # planar orderings, latitude beyond the pole, non-positive radius: rejected before any CUDA call
+    assert L.vecchia_plan_create_sphere(ll, 2, 1, vecchia.ORDER_MAXMIN, 0, None, 6371.0, None,
+                                        ctypes.byref(out)) == vecchia.EINVAL
+    assert L.vecchia_plan_create_sphere(ll, 2, 1, vecchia.ORDER_MORTON, 0, None, 6371.0, None,
+                                        ctypes.byref(out)) == vecchia.EINVAL
+    assert L.vecchia_plan_create_sphere(bad_lat, 2, 1, vecchia.ORDER_RANDOM, 0, None, 6371.0, None,
+                                        ctypes.byref(out)) == vecchia.EINVAL
+    assert L.vecchia_plan_create_sphere(ll, 2, 1, vecchia.ORDER_RANDOM, 0, None, 0.0, None,
+                                        ctypes.byref(out)) == vecchia.EINVAL
+    assert L.vecchia_plan_create_sphere(ll, 2, 1, vecchia.ORDER_RANDOM, 0, None, float("inf"), None,
+                                        ctypes.byref(out)) == vecchia.EINVAL
+
