@@ -17,6 +17,9 @@ What each function follows:
 * :func:`knn_rows` — Algorithm 1, nearest-neighbour loop: the m nearest
   *previously ordered* points, ties by index, brute force; :func:`knn_rows_sphere`
   the same on the sphere (keys: squared chord of unit vectors).
+* :func:`predict` — kriging at new locations from the m nearest observed ones (the
+  paper's prediction experiment, Sec. VI-C / Table III), by the Vecchia conditional
+  mean and variance.
 * :func:`gcd` — Sec. VI-C great-circle distance (haversine); ``radius=`` switches
   :func:`vecchia_rows` / :func:`loglik_exact` to it for (longitude, latitude) data.
 * :func:`vecchia_rows` / :func:`vecchia` — Sec. V-B: the Vecchia product of
@@ -84,6 +87,8 @@ def _load():
             "oracle_sphere_xyz": (None, [c_i64, _dp, _dp]),
             "oracle_gcd": (None, [c_i64, _dp, _dp, c_d, _dp]),
             "oracle_knn_rows_sphere": (c_int, [c_i64, _dp, c_i32, _i64p, c_i64, _i32p]),
+            "oracle_predict": (c_int, [c_i64, _dp, _dp, c_i64, _dp, c_i32, _dp, c_int, c_int, c_d, _dp, _dp,
+                                       _i32p]),
             "oracle_sum_columns": (None, [c_i64, c_i32, _dp, _dp]),
             "oracle_loglik_exact": (c_int, [c_i64, _dp, _dp, _dp, _dp, _dp, c_int, c_int, c_d]),
             "oracle_block_logdensity": (c_int, [c_i32, _dp, _dp, _dp]),
@@ -258,6 +263,30 @@ def vecchia_rows(xy_ordered, y_ordered, m: int, theta, rows=None, nbr=None, want
         raise OracleNotPD(int(bad[0]))
     res = out if want_grad else out[:, 0]
     return (res, mu_s) if return_mu_s else res
+
+
+def predict(xy_obs, y_obs, xy_new, m: int, theta, family=0, radius=None):
+    """Kriging from the m nearest observed locations: (mean, var, nbr) at each new point.
+
+    var is the conditional variance of y at the new point (nugget included); nbr holds
+    observed indices, nearest first, ties by index.  ``radius`` as in :func:`vecchia_rows`.
+    """
+    xo = _f64(xy_obs).reshape(-1, 2)
+    yo = _f64(y_obs)
+    xn = _f64(xy_new).reshape(-1, 2)
+    th = _f64(theta)
+    mean = np.empty(xn.shape[0])
+    var = np.empty(xn.shape[0])
+    nbr = np.empty((xn.shape[0], m), dtype=np.int32)
+    rc = _load().oracle_predict(xo.shape[0], _p(xo, _dp), _p(yo, _dp), xn.shape[0], _p(xn, _dp), int(m),
+                                _p(th, _dp), int(family), 0 if radius is None else 1,
+                                0.0 if radius is None else float(radius), _p(mean, _dp), _p(var, _dp),
+                                _p(nbr, _i32p))
+    if rc == 1:
+        raise ValueError("oracle_predict: invalid arguments")
+    if rc:
+        raise OracleNotPD(-1)
+    return mean, var, nbr
 
 
 def compensated_sum(v) -> np.ndarray:

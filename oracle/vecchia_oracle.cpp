@@ -531,6 +531,72 @@ int oracle_vecchia_rows(int64_t n, const double* xy, const double* y, int32_t m,
   return first_bad >= 0 ? 2 : 0;
 }
 
+// Prediction (kriging) at new locations from the m nearest OBSERVED locations (any of
+// them; ties by observed index): the conditional mean and variance of y at the new
+// point given y_J, by the same formulas as a Vecchia term (Sec. V-B) with y_new
+// unknown.  Metric 1: points are (longitude, latitude) in degrees, neighbours ranked
+// by the squared chord of unit vectors, covariance from great-circle distances.
+// Outputs: mean, var (n_new each), nbr (n_new x m observed indices).
+int oracle_predict(int64_t n_obs, const double* xy_obs, const double* y_obs, int64_t n_new, const double* xy_new,
+                   int32_t m, const double* theta, int family, int metric, double radius, double* mean,
+                   double* var, int32_t* nbr) {
+  if (m < 1 || m > n_obs) return 1;
+  std::vector<double> xyz_obs;
+  if (metric == 1) {
+    xyz_obs.resize(3 * (size_t)n_obs);
+    for (int64_t j = 0; j < n_obs; ++j) unit_vector(xy_obs + 2 * j, xyz_obs.data() + 3 * j);
+  }
+  int bad = 0;
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int64_t k = 0; k < n_new; ++k) {
+    // m nearest observed points, lexicographic (key, index), brute force
+    std::vector<double> bd(m);
+    std::vector<int64_t> bj(m);
+    double q3[3];
+    if (metric == 1) unit_vector(xy_new + 2 * k, q3);
+    int cnt = 0;
+    for (int64_t j = 0; j < n_obs; ++j) {
+      const double d = metric == 1 ? chord2(q3, xyz_obs.data() + 3 * j) : dist2(xy_new + 2 * k, xy_obs + 2 * j);
+      if (cnt == m) {
+        if (!(d < bd[m - 1])) continue;
+        --cnt;
+      }
+      int p = cnt;
+      while (p > 0 && (d < bd[p - 1])) { bd[p] = bd[p - 1]; bj[p] = bj[p - 1]; --p; }
+      bd[p] = d; bj[p] = j; ++cnt;
+    }
+    // mu = Sigma_kJ Sigma_JJ^-1 y_J and s = Sigma_kk - Sigma_kJ Sigma_JJ^-1 Sigma_Jk on a
+    // local array (the m neighbours, then the new point); s may be 0 (interpolation).
+    const double sigma2 = theta[0], beta = theta[1], nu = theta[2], tau2 = theta[3];
+    std::vector<double> lxy(2 * (size_t)(m + 1)), SJ((size_t)m * m), LJ((size_t)m * m), v(m), w(m);
+    for (int p = 0; p < m; ++p) {
+      lxy[2 * p] = xy_obs[2 * bj[p]];
+      lxy[2 * p + 1] = xy_obs[2 * bj[p] + 1];
+      nbr[(size_t)k * m + p] = (int32_t)bj[p];
+    }
+    lxy[2 * m] = xy_new[2 * k];
+    lxy[2 * m + 1] = xy_new[2 * k + 1];
+    for (int p = 0; p < m; ++p) {
+      for (int q = 0; q < m; ++q)
+        SJ[(size_t)p * m + q] = p == q ? sigma2 + tau2 : cov(family, point_dist(lxy.data(), p, q, metric, radius),
+                                                              sigma2, beta, nu);
+      v[p] = cov(family, point_dist(lxy.data(), p, m, metric, radius), sigma2, beta, nu);
+    }
+    if (!cholesky(m, SJ.data(), LJ.data())) {
+#pragma omp atomic write
+      bad = 1;
+      mean[k] = var[k] = std::numeric_limits<double>::quiet_NaN();
+      continue;
+    }
+    chol_solve(m, LJ.data(), v.data(), w.data());
+    double mu = 0.0, vw = 0.0;
+    for (int p = 0; p < m; ++p) { mu += w[p] * y_obs[bj[p]]; vw += w[p] * v[p]; }
+    mean[k] = mu;
+    var[k] = sigma2 + tau2 - vw;
+  }
+  return bad ? 2 : 0;
+}
+
 // Neumaier-compensated sum of `cols` interleaved columns, in row order.
 void oracle_sum_columns(int64_t nrows, int32_t cols, const double* v, double* out) {
   for (int c = 0; c < cols; ++c) {

@@ -398,3 +398,57 @@ def test_sphere_full_conditioning_equals_dense(oracle_mod, family, theta):
     assert _rel(va[0], ex) < 1e-10
     np.testing.assert_allclose(va[1:], gex, rtol=1e-8, atol=1e-8 * np.abs(gex).max())
 
+
+
+# ----------------------------------------------------------------- prediction (kriging)
+def test_predict_interpolates_observed_points(oracle_mod):
+    # tau2 = 0: at an observed location the conditional mean is y there and the variance 0.
+    xy = datagen.uniform_locations(400, 51)
+    theta = (1.3, 0.1, 1.5, 0.0)
+    y = datagen.field_dense(xy, theta, 52)
+    mean, var, nbr = oracle_mod.predict(xy, y, xy[:40], 12, theta)
+    np.testing.assert_allclose(mean, y[:40], rtol=0, atol=1e-12)
+    assert np.all(np.abs(var) <= 1e-12)
+    assert np.all(nbr[:, 0] == np.arange(40))
+
+
+@pytest.mark.parametrize("theta", [(1.0, 0.1, 0.5, 0.05), (1.5, 0.06, 2.5, 0.01)])
+def test_predict_with_all_points_is_dense_kriging(oracle_mod, theta):
+    n, k = 150, 30
+    xy = datagen.uniform_locations(n + k, 53)
+    y = datagen.field_dense(xy[:n], theta, 54)
+    mean, var, _ = oracle_mod.predict(xy[:n], y, xy[n:], n, theta)
+    S = _cov_scipy(xy[:n], theta)
+    s2, b, nu, t2 = theta
+    d = np.sqrt(((xy[n:, None] - xy[None, :n]) ** 2).sum(-1))
+    Kx = s2 * 2 ** (1 - nu) / sp_gamma(nu) * (d / b) ** nu * kv(nu, d / b)
+    want_mean = Kx @ np.linalg.solve(S, y)
+    want_var = s2 + t2 - np.einsum("ij,ji->i", Kx, np.linalg.solve(S, Kx.T))
+    np.testing.assert_allclose(mean, want_mean, rtol=1e-9, atol=1e-11)
+    np.testing.assert_allclose(var, want_var, rtol=1e-8, atol=1e-11)
+
+
+def test_predict_neighbours_brute_force(oracle_mod):
+    xy = datagen.uniform_locations(2000, 55)
+    new = datagen.uniform_locations(50, 56)
+    _, _, nbr = oracle_mod.predict(xy, np.zeros(2000), new, 15, (1.0, 0.1, 0.5, 0.01))
+    for k in range(50):
+        dx, dy = xy[:, 0] - new[k, 0], xy[:, 1] - new[k, 1]
+        d2 = dx * dx + dy * dy
+        assert list(nbr[k]) == list(np.lexsort((np.arange(2000), d2))[:15])
+
+
+def test_predict_on_sphere_is_dense_kriging(oracle_mod):
+    n, k = 120, 20
+    ll = datagen.sphere_locations(n + k, 57)
+    theta = (1.0, 70.0, 0.5, 0.02)
+    u = datagen.sphere_coords(ll, 1.0)
+    d = 2.0 * R_EARTH * np.arcsin(np.clip(np.linalg.norm(u[:, None] - u[None], axis=-1) / 2.0, 0, 1))
+    C = theta[0] * np.exp(-d / theta[1])  # nu = 1/2: the exponential
+    y = np.linalg.cholesky(C[:n, :n] + theta[3] * np.eye(n)) @ datagen.rng(58).standard_normal(n)
+    mean, var, _ = oracle_mod.predict(ll[:n], y, ll[n:], n, theta, radius=R_EARTH)
+    S = C[:n, :n] + theta[3] * np.eye(n)
+    Kx = C[n:, :n]
+    np.testing.assert_allclose(mean, Kx @ np.linalg.solve(S, y), rtol=1e-9, atol=1e-11)
+    np.testing.assert_allclose(var, theta[0] + theta[3] - np.einsum("ij,ji->i", Kx, np.linalg.solve(S, Kx.T)),
+                               rtol=1e-8, atol=1e-11)
