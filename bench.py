@@ -218,6 +218,73 @@ def run_m_sweep(V, dev, peak_tflops, n=250_000, ms=(10, 30, 60, 90, 120, 150)):
     return rows
 
 
+def run_sphere(V, dev, peak_tflops, n=250_000, m=60):
+    """Great-circle workload (Sec. VI-C stand-in): n (longitude, latitude) points on a
+    15 x 15 degree patch, radius 6371 km, random ordering, Matérn nu = 0.5 with
+    beta = 50 km and a 3-D random-Fourier-feature field in chordal distance."""
+    import torch
+    from paper_2403_07412_gb300 import datagen
+
+    seed = datagen.BASE_SEED + 7
+    radius = 6371.0
+    ll = datagen.sphere_locations(n, seed)
+    theta = (1.0, 50.0, 0.5, 0.02)
+    y = torch.as_tensor(datagen.field_rff(datagen.sphere_coords(ll, radius), theta, seed + 1000, device=dev),
+                        device=dev)
+    t0 = time.perf_counter()
+    plan = V.Plan(ll, m, order=V.ORDER_RANDOM, seed=seed, radius=radius)
+    torch.cuda.synchronize()
+    plan_s = time.perf_counter() - t0
+    out = torch.empty(4, dtype=torch.float64, device=dev)
+    row = {"workload": f"{n} lon/lat points on a 15x15-degree patch, great-circle distance (r = 6371 km), "
+                       f"random ordering, m = {m}, Matern nu = 0.5, beta = 50 km",
+           "plan_seconds": round(plan_s, 3)}
+    for name, fn, grad in (("fwd", V.vecchia_loglik, False), ("grad", V.vecchia_loglik_grad, True)):
+        fn(plan, y, theta, out=out)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(3):
+            fn(plan, y, theta, out=out)
+        e1.record()
+        torch.cuda.synchronize()
+        ms_call = e0.elapsed_time(e1) / 3
+        tf = la_flops(n, m, grad) / (ms_call * 1e-3) / 1e12
+        row[name] = {"ms": round(ms_call, 3), "locations_per_s": n / (ms_call * 1e-3),
+                     "frac_of_fp64_peak": round(tf / peak_tflops, 4)}
+    plan.close()
+    return row
+
+
+def run_predict(V, dev, n=250_000, n_new=25_000, m=30):
+    """Kriging (the paper's prediction experiment, Sec. VI-C: 250K training and 25K test
+    locations) on a synthetic field: predictions per second through vecchia_predict
+    (conditioning-set search included) and the mean squared prediction error against
+    the held-out values."""
+    import torch
+    from paper_2403_07412_gb300 import datagen
+
+    seed = datagen.BASE_SEED + 8
+    theta = (1.0, 0.01, 1.5, 0.01)
+    xy = datagen.uniform_locations(n + n_new, seed)
+    y = datagen.field_rff(xy, theta, seed + 1000, device=dev)
+    plan = V.Plan(xy[:n], m, order=V.ORDER_RANDOM, seed=seed)
+    yd = torch.as_tensor(y[:n], device=dev)
+    V.vecchia_predict(plan, xy[n:n + 1000], yd, theta)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    mean, var = V.vecchia_predict(plan, xy[n:], yd, theta)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    err = mean.cpu().numpy() - y[n:]
+    plan.close()
+    return {"workload": f"{n} observed / {n_new} new uniform locations, m = {m}, Matern nu = 1.5, beta = 0.01",
+            "predictions_per_s": n_new / dt, "seconds": round(dt, 4),
+            "mspe": float(np.mean(err ** 2)), "field_variance": float(np.var(y[n:])),
+            "mean_predictive_var": float(var.mean().item())}
+
+
 def cpu_baseline(xy, y, theta, m, budget_s):
     """The oracle, as it stands, on a bounded random sample of rows of the same workload
     (its own random ordering and brute-force conditioning sets; neighbour search untimed)."""
@@ -319,6 +386,8 @@ def main():
     ap.add_argument("--fwd", action="store_true", help="time the forward-only kernel instead")
     ap.add_argument("--no-batched", action="store_true", help="skip the many-field batched measurement")
     ap.add_argument("--no-m-sweep", action="store_true", help="skip the conditioning-size sweep")
+    ap.add_argument("--no-sphere", action="store_true", help="skip the great-circle workload")
+    ap.add_argument("--no-predict", action="store_true", help="skip the kriging workload")
     ap.add_argument("--batched-scale", type=float, default=1.0, help="scale of the batched fields' sizes")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -502,6 +571,10 @@ def main():
         line["batched"] = run_batched(V, dev, peak, scale=args.batched_scale)
     if not args.no_m_sweep:
         line["m_sweep"] = run_m_sweep(V, dev, peak)
+    if not args.no_sphere:
+        line["sphere"] = run_sphere(V, dev, peak)
+    if not args.no_predict:
+        line["predict"] = run_predict(V, dev)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(xy, y, theta, m, args.cpu_budget)
     print(json.dumps(line), flush=True)

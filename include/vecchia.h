@@ -280,6 +280,29 @@ int vecchia_autotune(vecchia_plan_t plan, const double* y_dev, const double thet
                      int32_t* lanes_out, int32_t* warps_out, void* stream);
 
 /*
+ * vecchia_predict — kriging at new locations (the prediction step of the paper's
+ * real-data study, Sec. VI-C / Table III) from the plan's observed data: for each new
+ * point, its m nearest OBSERVED points (any of the plan's n points; ties to the lower
+ * original index; Euclidean or great-circle as the plan) condition it, and
+ *   mean = Sigma_kJ Sigma_JJ^{-1} y_J,   var = sigma2 + tau2 - Sigma_kJ Sigma_JJ^{-1} Sigma_Jk,
+ * the Vecchia conditional of Sec. V-B with y at the new point unknown (var includes the
+ * nugget: it is the predictive variance of an observation there).
+ *   xy_new_host : n_new x 2 doubles, host (the plan's coordinate kind), copied.
+ *   y_dev       : n doubles, device, ORIGINAL order (as for vecchia_loglik).
+ *   theta       : (sigma2, beta, nu, tau2), host; the plan's covariance family.
+ *   mean_dev    : n_new doubles, device, written.  var_dev: n_new doubles or NULL.
+ *   nbr_host    : optional n_new x m int32, host: the conditioning sets (original
+ *                 indices, nearest first).
+ * Synchronises `stream` before returning (temporary buffers are freed).  m must be at
+ * most VECCHIA_MAX_M_WARP and at most n.  A location whose neighbour block is not
+ * positive definite gets NaN and is reported through vecchia_last_error_location, with
+ * status VECCHIA_OK (the other predictions stand).  EINVAL: non-finite or (sphere)
+ * out-of-range coordinates, bad theta, m > VECCHIA_MAX_M_WARP or m > n, n_new < 1.
+ */
+int vecchia_predict(vecchia_plan_t plan, const double* xy_new_host, int64_t n_new, const double* y_dev,
+                    const double theta[4], double* mean_dev, double* var_dev, int32_t* nbr_host, void* stream);
+
+/*
  * vecchia_last_error_location — synchronises the stream of the plan's last call and
  * reports the first ordered location whose block was not positive definite in that
  * call (*loc = -1 if none).  Returns ENOTPD if there was one, else OK.

@@ -92,7 +92,7 @@ __device__ __forceinline__ void run_item(const FieldDesc& fd, int64_t tile, cons
   for (int64_t b = i0; b < i1; b += NL) {
     const int64_t i = b + grp;
     const bool active = i < i1;
-    process_location<GRAD, G>(active ? i : b, active, F, S, sched, pairs, area, tab, mc, tc, acc, false, nullptr,
+    process_location<GRAD, G, false>(active ? i : b, active, F, S, sched, pairs, area, tab, mc, tc, acc, false, nullptr,
                               a.errloc, sub);
   }
   write_partial<G>(acc, out, lane);

@@ -58,13 +58,13 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return s;
 }
 
-template <bool GRAD>
+template <bool GRAD, bool SPHERE>
 __global__ void __launch_bounds__(kCtaThreadsMax) vecchia_big_kernel(const BigArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int m = a.m, K = m + 1;
   const int NTd = (K + 1) * (K + 2) / 2, NP = K * (K - 1) / 2;
   double* A = reinterpret_cast<double*>(smem);
-  const bool sphere = a.metric == 1;
+  constexpr bool sphere = SPHERE;
   float2* CX = reinterpret_cast<float2*>(A + align_up(NTd, 2));
   float2* CY = CX + align_up(K + 1, 2);
   float2* CZ = sphere ? CY + align_up(K + 1, 2) : CY;
@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(kCtaThreadsMax) vecchia_big_kernel(const BigAr
   FieldView F;  // the distance fields pair_u reads
   F.sphere = sphere;
   F.xyz = a.xyz;
-  if (sphere) {
+  if constexpr (SPHERE) {
     const double k = 2.0 * a.radius * tc.inv_len;
     F.k2d = k * k;
     F.k2 = d2f_pair(F.k2d);
@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(kCtaThreadsMax) vecchia_big_kernel(const BigAr
         double xv = 0.0, yv = 0.0, zv = 0.0, fv = 0.0;
         if (p < mi) {
           const int j = row[p];
-          if (sphere) {
+          if constexpr (SPHERE) {
             xv = a.xyz[3 * j] - a.xyz[3 * js];
             yv = a.xyz[3 * j + 1] - a.xyz[3 * js + 1];
             zv = a.xyz[3 * j + 2] - a.xyz[3 * js + 2];
@@ -118,13 +118,13 @@ __global__ void __launch_bounds__(kCtaThreadsMax) vecchia_big_kernel(const BigAr
         YV[p] = fv;
         CX[p] = d2f_pair(xv);
         CY[p] = d2f_pair(yv);
-        if (sphere) CZ[p] = d2f_pair(zv);
+        if constexpr (SPHERE) CZ[p] = d2f_pair(zv);
       }
     }
     if (tid == 0) {
       CX[m] = make_float2(0.0f, 0.0f);
       CY[m] = make_float2(0.0f, 0.0f);
-      CZ[m] = make_float2(0.0f, 0.0f);
+      if constexpr (SPHERE) CZ[m] = make_float2(0.0f, 0.0f);
       YV[m] = a.yf[js];
     }
     __syncthreads();
@@ -145,8 +145,8 @@ __global__ void __launch_bounds__(kCtaThreadsMax) vecchia_big_kernel(const BigAr
       const bool ok0 = c0 < mi && (r0 < mi || r0 == m);
       const bool ok1 = has1 && c1 < mi && (r1 < mi || r1 == m);
       float u0h, u0l, u1h, u1l;
-      pair_u(F, CX, CY, CZ, r0, c0, u0h, u0l);
-      pair_u(F, CX, CY, CZ, r1, c1, u1h, u1l);
+      pair_u<SPHERE>(F, CX, CY, CZ, r0, c0, u0h, u0l);
+      pair_u<SPHERE>(F, CX, CY, CZ, r1, c1, u1h, u1l);
       const double val0 = rho_df(u0h, u0l, a.tab, mc), val1 = rho_df(u1h, u1l, a.tab, mc);
       A[tri_off(K, c0) + r0 - c0] = ok0 ? val0 : 0.0;
       if (has1) A[tri_off(K, c1) + r1 - c1] = ok1 ? val1 : 0.0;
@@ -274,7 +274,7 @@ __global__ void __launch_bounds__(kCtaThreadsMax) vecchia_big_kernel(const BigAr
         const int v0 = tri_root(q0);
         const int c0 = K - 2 - v0, r0 = c0 + 1 + (q0 - v0 * (v0 + 1) / 2);
         float uh, ul, hh, hl;
-        pair_u(F, CX, CY, CZ, r0, c0, uh, ul);
+        pair_u<SPHERE>(F, CX, CY, CZ, r0, c0, uh, ul);
         h_df(uh, ul, a.tab, mc, hh, hl);
         beta_pair_add(WHf[r0], WHf[c0], GVf[r0], GVf[c0], hh, hl, pbh, pbl);
       }
@@ -326,7 +326,8 @@ int big_config(int K, bool grad, int* blocks, int* threads, int* smem, bool sphe
   VECCHIA_CUDA_TRY(cudaGetDevice(&dev));
   VECCHIA_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   *smem = big_smem_bytes(K, sphere);
-  auto kern = grad ? vecchia_big_kernel<true> : vecchia_big_kernel<false>;
+  auto kern = grad ? (sphere ? vecchia_big_kernel<true, true> : vecchia_big_kernel<true, false>)
+                   : (sphere ? vecchia_big_kernel<false, true> : vecchia_big_kernel<false, false>);
   VECCHIA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, *smem));
   const char* e = getenv("VECCHIA_CTA_THREADS");
   const int forced = e ? atoi(e) : 0;
@@ -348,8 +349,14 @@ int big_config(int K, bool grad, int* blocks, int* threads, int* smem, bool sphe
 }
 
 void launch_big(bool grad, int blocks, int threads, int smem, const BigArgs& a, cudaStream_t s) {
-  if (grad) vecchia_big_kernel<true><<<blocks, threads, smem, s>>>(a);
-  else vecchia_big_kernel<false><<<blocks, threads, smem, s>>>(a);
+  const bool sph = a.metric == 1;
+  if (grad) {
+    if (sph) vecchia_big_kernel<true, true><<<blocks, threads, smem, s>>>(a);
+    else vecchia_big_kernel<true, false><<<blocks, threads, smem, s>>>(a);
+  } else {
+    if (sph) vecchia_big_kernel<false, true><<<blocks, threads, smem, s>>>(a);
+    else vecchia_big_kernel<false, false><<<blocks, threads, smem, s>>>(a);
+  }
 }
 
 }  // namespace vecchia

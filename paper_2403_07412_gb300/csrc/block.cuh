@@ -145,6 +145,11 @@ struct FieldView {
   bool sphere = false;
   float2 k2 = make_float2(0.0f, 0.0f);
   double k2d = 0.0;
+  // prediction: every location has m conditioning points (all observed points qualify),
+  // y of the location itself is 0 (unknown), and the conditional mean and variance are
+  // written to pmean / pvar (n each) instead of likelihood terms
+  double* pmean = nullptr;
+  double* pvar = nullptr;
 };
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -267,11 +272,13 @@ __device__ __forceinline__ void sphere_u_df(float ch, float cl, const FieldView&
   df_mul(F.k2.x, F.k2.y, vh, vl, uh, ul);
 }
 
-// u of the pair (r, c) of the block, plane or sphere.
+// u of the pair (r, c) of the block, plane or sphere (a compile-time choice, so that the
+// planar kernels carry no trace of the sphere path).
+template <bool SPHERE>
 __device__ __forceinline__ void pair_u(const FieldView& F, const float2* __restrict__ CX,
                                        const float2* __restrict__ CY, const float2* __restrict__ CZ, int r, int c,
                                        float& uh, float& ul) {
-  if (F.sphere) {
+  if constexpr (SPHERE) {
     float ch, cl;
     sq_chord_df(CX[r], CX[c], CY[r], CY[c], CZ[r], CZ[c], ch, cl);
     sphere_u_df(ch, cl, F, uh, ul);
@@ -298,7 +305,7 @@ __device__ __forceinline__ void beta_pair_add(float2 wr, float2 wc, float2 gr, f
   pbl = __fsub_rn(e, __fsub_rn(pbh, s));
 }
 
-template <bool GRAD, int G>
+template <bool GRAD, int G, bool SPHERE>
 __device__ __forceinline__ void process_location(int64_t i, bool active, const FieldView& F, const SchedSize& S,
                                                  const uint16_t* __restrict__ sched,
                                                  const uint32_t* __restrict__ pairs, const WarpArea& W,
@@ -314,7 +321,7 @@ __device__ __forceinline__ void process_location(int64_t i, bool active, const F
   float2* __restrict__ CZ = W.CZ;
   double* __restrict__ YV = W.YV;
   double* __restrict__ TV = W.TV;
-  const int mi = i < m ? (int)i : m;
+  const int mi = (i < m && !F.pmean) ? (int)i : m;
   const int32_t* __restrict__ row = F.nbr + i * m;
   const int js = F.self[i];
   const double2 ps = F.xy[js];
@@ -326,7 +333,7 @@ __device__ __forceinline__ void process_location(int64_t i, bool active, const F
       double xv = 0.0, yv = 0.0, zv = 0.0, fv = 0.0;
       if (p < mi) {
         const int j = row[p];
-        if (F.sphere) {  // unit-vector offsets; the length scale enters through K2
+        if constexpr (SPHERE) {  // unit-vector offsets; the length scale enters through K2
           xv = F.xyz[3 * j] - F.xyz[3 * js];
           yv = F.xyz[3 * j + 1] - F.xyz[3 * js + 1];
           zv = F.xyz[3 * j + 2] - F.xyz[3 * js + 2];
@@ -340,13 +347,13 @@ __device__ __forceinline__ void process_location(int64_t i, bool active, const F
       YV[p] = fv;
       CX[p] = d2f_pair(xv);
       CY[p] = d2f_pair(yv);
-      if (F.sphere) CZ[p] = d2f_pair(zv);
+      if constexpr (SPHERE) CZ[p] = d2f_pair(zv);
     }
   }
   if (sub == 0) {
     CX[m] = make_float2(0.0f, 0.0f);
     CY[m] = make_float2(0.0f, 0.0f);
-    CZ[m] = make_float2(0.0f, 0.0f);
+    if constexpr (SPHERE) CZ[m] = make_float2(0.0f, 0.0f);
     YV[m] = F.yf[js];
   }
   __syncwarp();
@@ -368,8 +375,8 @@ __device__ __forceinline__ void process_location(int64_t i, bool active, const F
     const bool v0 = c0 < mi && (r0 < mi || r0 == m);
     const bool v1 = has1 && c1 < mi && (r1 < mi || r1 == m);
     float u0h, u0l, u1h, u1l;
-    pair_u(F, CX, CY, CZ, r0, c0, u0h, u0l);
-    pair_u(F, CX, CY, CZ, r1, c1, u1h, u1l);
+    pair_u<SPHERE>(F, CX, CY, CZ, r0, c0, u0h, u0l);
+    pair_u<SPHERE>(F, CX, CY, CZ, r1, c1, u1h, u1l);
     const double val0 = rho_df(u0h, u0l, tab, mc), val1 = rho_df(u1h, u1l, tab, mc);
     A[w0 >> 16] = v0 ? val0 : 0.0;
     if (has1) A[w1 >> 16] = v1 ? val1 : 0.0;
@@ -444,7 +451,14 @@ __device__ __forceinline__ void process_location(int64_t i, bool active, const F
       acc.count += 1;
     } else {
       acc.Q.add(nan);
-      if (sub == 0) atomicMin(errloc, (unsigned long long)i);
+      if (sub == 0 && !F.pmean) atomicMin(errloc, (unsigned long long)i);
+    }
+    if (F.pmean && sub == 0) {
+      // y_i = 0 here, so rr = -mu; a variance of 0 (prediction at an observed point
+      // without nugget) is valid, so only a failed neighbour factorisation gives NaN
+      F.pmean[i] = ok ? -rr : nan;
+      if (F.pvar) F.pvar[i] = ok ? fmax(s, 0.0) : nan;
+      if (!ok) atomicMin(errloc, (unsigned long long)i);
     }
   }
   // per-location terms (test and inspection path) pay for their own log
@@ -527,8 +541,8 @@ __device__ __forceinline__ void process_location(int64_t i, bool active, const F
     const int r0 = w0 & 0xFF, c0 = (w0 >> 8) & 0xFF;
     const int r1 = w1 & 0xFF, c1 = (w1 >> 8) & 0xFF;
     float u0h, u0l, u1h, u1l;
-    pair_u(F, CX, CY, CZ, r0, c0, u0h, u0l);
-    pair_u(F, CX, CY, CZ, r1, c1, u1h, u1l);
+    pair_u<SPHERE>(F, CX, CY, CZ, r0, c0, u0h, u0l);
+    pair_u<SPHERE>(F, CX, CY, CZ, r1, c1, u1h, u1l);
     float h0h, h0l, h1h, h1l;
     h_df(u0h, u0l, tab, mc, h0h, h0l);
     h_df(u1h, u1l, tab, mc, h1h, h1l);

@@ -59,6 +59,8 @@ struct LikArgs {
   const double* __restrict__ xyz = nullptr;  // n x 3 unit vectors (sphere plans)
   int metric = 0;                    // 0 plane, 1 sphere
   double radius = 1.0;
+  double* pmean = nullptr;           // prediction outputs (n), see FieldView
+  double* pvar = nullptr;
 };
 
 // Shared-memory layout for block size K (= m + 1), G lanes per location (32/G locations
@@ -73,12 +75,12 @@ struct SmemLayout {
   __host__ __device__ int bytes(int W) const { return S.sched_bytes + S.pairs_bytes + W * per_warp_doubles * 8; }
 };
 
-template <bool GRAD, int G>
+template <bool GRAD, int G, bool SPHERE>
 __global__ void __launch_bounds__(384) vecchia_lik_kernel(const LikArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int NL = 32 / G;
   const int K = a.m + 1;
-  const bool sphere = a.metric == 1;
+  constexpr bool sphere = SPHERE;
   const SmemLayout L(K, GRAD, G, sphere);
   uint16_t* sched = reinterpret_cast<uint16_t*>(smem);
   uint32_t* pairs = reinterpret_cast<uint32_t*>(smem + L.S.sched_bytes);
@@ -101,7 +103,9 @@ __global__ void __launch_bounds__(384) vecchia_lik_kernel(const LikArgs a) {
   F.self = a.self;
   F.n = a.n;
   F.m = a.m;
-  if (sphere) {
+  F.pmean = a.pmean;
+  F.pvar = a.pvar;
+  if constexpr (SPHERE) {
     F.sphere = true;
     F.xyz = a.xyz;
     const double k = 2.0 * a.radius * tc.inv_len;
@@ -117,7 +121,7 @@ __global__ void __launch_bounds__(384) vecchia_lik_kernel(const LikArgs a) {
     const bool active = i < a.n;
     const int64_t ii = active ? i : base;
     double* trow = terms_mode ? a.terms + ii * (GRAD ? 4 : 1) : nullptr;
-    process_location<GRAD, G>(ii, active, F, L.S, sched, pairs, area, a.tab, mc, tc, acc, terms_mode, trow,
+    process_location<GRAD, G, SPHERE>(ii, active, F, L.S, sched, pairs, area, a.tab, mc, tc, acc, terms_mode, trow,
                               a.errloc, sub);
   }
   write_partial<G>(acc, a.partial + gw * 4, lane);
@@ -152,14 +156,16 @@ struct LaunchCfg {
   int G = 32, W = 4, blocks = 0, smem = 0;
 };
 
-template <bool GRAD, int G>
-void* kernel_ptr() {
-  return reinterpret_cast<void*>(vecchia_lik_kernel<GRAD, G>);
+template <bool GRAD, bool SPHERE>
+void* kernel_ptr(int G) {
+  if (G == 8) return reinterpret_cast<void*>(vecchia_lik_kernel<GRAD, 8, SPHERE>);
+  if (G == 16) return reinterpret_cast<void*>(vecchia_lik_kernel<GRAD, 16, SPHERE>);
+  return reinterpret_cast<void*>(vecchia_lik_kernel<GRAD, 32, SPHERE>);
 }
 
-void* lik_kernel(bool grad, int G) {
-  if (grad) return G == 8 ? kernel_ptr<true, 8>() : G == 16 ? kernel_ptr<true, 16>() : kernel_ptr<true, 32>();
-  return G == 8 ? kernel_ptr<false, 8>() : G == 16 ? kernel_ptr<false, 16>() : kernel_ptr<false, 32>();
+void* lik_kernel(bool grad, int G, bool sphere) {
+  if (grad) return sphere ? kernel_ptr<true, true>(G) : kernel_ptr<true, false>(G);
+  return sphere ? kernel_ptr<false, true>(G) : kernel_ptr<false, false>(G);
 }
 
 // Lanes per location chosen when no tuning result exists: small blocks share a warp.
@@ -202,7 +208,7 @@ int shape_for(int K, bool grad, int G, int forced_W, LaunchCfg* cfg, bool sphere
   VECCHIA_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   VECCHIA_CUDA_TRY(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   const SmemLayout L(K, grad, G, sphere);
-  void* kern = lik_kernel(grad, G);
+  void* kern = lik_kernel(grad, G, sphere);
   int best_warps = -1;
   for (int W : {12, 11, 10, 9, 8, 6, 4, 2, 1}) {
     if (forced_W > 0 && W != forced_W) continue;
@@ -242,16 +248,22 @@ int pick_config(int K, bool grad, LaunchCfg* cfg, bool sphere = false) {
   return shape_for(K, grad, G, W, cfg, sphere);
 }
 
-void launch_lik(const LaunchCfg& cfg, bool grad, const LikArgs& a, cudaStream_t stream) {
+template <bool SPHERE>
+void launch_lik_m(const LaunchCfg& cfg, bool grad, const LikArgs& a, cudaStream_t stream) {
   if (grad) {
-    if (cfg.G == 8) vecchia_lik_kernel<true, 8><<<cfg.blocks, cfg.W * 32, cfg.smem, stream>>>(a);
-    else if (cfg.G == 16) vecchia_lik_kernel<true, 16><<<cfg.blocks, cfg.W * 32, cfg.smem, stream>>>(a);
-    else vecchia_lik_kernel<true, 32><<<cfg.blocks, cfg.W * 32, cfg.smem, stream>>>(a);
+    if (cfg.G == 8) vecchia_lik_kernel<true, 8, SPHERE><<<cfg.blocks, cfg.W * 32, cfg.smem, stream>>>(a);
+    else if (cfg.G == 16) vecchia_lik_kernel<true, 16, SPHERE><<<cfg.blocks, cfg.W * 32, cfg.smem, stream>>>(a);
+    else vecchia_lik_kernel<true, 32, SPHERE><<<cfg.blocks, cfg.W * 32, cfg.smem, stream>>>(a);
   } else {
-    if (cfg.G == 8) vecchia_lik_kernel<false, 8><<<cfg.blocks, cfg.W * 32, cfg.smem, stream>>>(a);
-    else if (cfg.G == 16) vecchia_lik_kernel<false, 16><<<cfg.blocks, cfg.W * 32, cfg.smem, stream>>>(a);
-    else vecchia_lik_kernel<false, 32><<<cfg.blocks, cfg.W * 32, cfg.smem, stream>>>(a);
+    if (cfg.G == 8) vecchia_lik_kernel<false, 8, SPHERE><<<cfg.blocks, cfg.W * 32, cfg.smem, stream>>>(a);
+    else if (cfg.G == 16) vecchia_lik_kernel<false, 16, SPHERE><<<cfg.blocks, cfg.W * 32, cfg.smem, stream>>>(a);
+    else vecchia_lik_kernel<false, 32, SPHERE><<<cfg.blocks, cfg.W * 32, cfg.smem, stream>>>(a);
   }
+}
+
+void launch_lik(const LaunchCfg& cfg, bool grad, const LikArgs& a, cudaStream_t stream) {
+  if (a.metric == 1) launch_lik_m<true>(cfg, grad, a, stream);
+  else launch_lik_m<false>(cfg, grad, a, stream);
 }
 }  // namespace
 
@@ -367,6 +379,100 @@ int launch_loglik(Plan* p, const double* y_dev, const double* theta, bool grad, 
   int rc = pick_config(p->m + 1, grad, &cfg, p->metric == 1);
   if (rc) return rc;
   return launch_with(p, y_dev, theta, grad, cfg, out_dev, terms_dev, stream);
+}
+
+int knn_predict(Plan* p, const double* xy_new_host, int64_t n_new, int32_t* d_nbr_new, std::vector<double>* xyz_new_out,
+                cudaStream_t stream);
+
+// Kriging at new points (vecchia_predict): conditioning sets from knn_predict, then the
+// likelihood kernel over the new points with the observed and new coordinates side by
+// side (observed first, so the sets' original indices address them), y = 0 at the new
+// points and the prediction outputs in place of the likelihood sums.
+int predict(Plan* p, const double* xy_new_host, int64_t n_new, const double* y_dev, const double* theta,
+            double* mean_dev, double* var_dev, int32_t* nbr_host, cudaStream_t stream) {
+  if (!p || !xy_new_host || n_new < 1 || n_new > 2147483647LL - p->n || !y_dev || !mean_dev ||
+      !theta_ok_family(theta, p->family))
+    return VECCHIA_EINVAL;
+  if (p->m > kMaxMWarp || p->m > p->n) return VECCHIA_EINVAL;
+  for (int64_t k = 0; k < 2 * n_new; ++k)
+    if (!std::isfinite(xy_new_host[k])) return VECCHIA_EINVAL;
+  if (p->metric == 1)
+    for (int64_t k = 0; k < n_new; ++k)
+      if (!(fabs(xy_new_host[2 * k + 1]) <= 90.0)) return VECCHIA_EINVAL;
+  const int64_t n = p->n, nt = n + n_new, m = p->m;
+  int32_t* d_nbr = nullptr;
+  int32_t* d_self = nullptr;
+  double *d_xy = nullptr, *d_y = nullptr, *d_xyz = nullptr;
+  int rc = VECCHIA_OK;
+  if (cudaMalloc(&d_nbr, sizeof(int32_t) * n_new * m) != cudaSuccess ||
+      cudaMalloc(&d_self, sizeof(int32_t) * n_new) != cudaSuccess ||
+      cudaMalloc(&d_xy, sizeof(double) * 2 * nt) != cudaSuccess || cudaMalloc(&d_y, sizeof(double) * nt) != cudaSuccess ||
+      (p->metric == 1 && cudaMalloc(&d_xyz, sizeof(double) * 3 * nt) != cudaSuccess))
+    rc = VECCHIA_ENOMEM;
+  std::vector<double> xyz_new;
+  if (!rc) rc = knn_predict(p, xy_new_host, n_new, d_nbr, &xyz_new, stream);
+  std::vector<int32_t> self(n_new);
+  for (int64_t k = 0; k < n_new; ++k) self[k] = (int32_t)(n + k);
+  auto cp = [&](void* dst, const void* src, size_t bytes, cudaMemcpyKind kind) {
+    if (!rc && cudaMemcpyAsync(dst, src, bytes, kind, stream) != cudaSuccess) rc = VECCHIA_ECUDA;
+  };
+  cp(d_self, self.data(), sizeof(int32_t) * n_new, cudaMemcpyHostToDevice);
+  cp(d_xy, p->d_xy, sizeof(double) * 2 * n, cudaMemcpyDeviceToDevice);
+  cp(d_xy + 2 * n, xy_new_host, sizeof(double) * 2 * n_new, cudaMemcpyHostToDevice);
+  cp(d_y, y_dev, sizeof(double) * n, cudaMemcpyDeviceToDevice);
+  if (!rc && cudaMemsetAsync(d_y + n, 0, sizeof(double) * n_new, stream) != cudaSuccess) rc = VECCHIA_ECUDA;
+  if (p->metric == 1) {
+    cp(d_xyz, p->d_xyz, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice);
+    cp(d_xyz + 3 * n, xyz_new.data(), sizeof(double) * 3 * n_new, cudaMemcpyHostToDevice);
+  }
+  LaunchCfg cfg;
+  if (!rc) rc = pick_config((int)m + 1, false, &cfg, p->metric == 1);
+  const int64_t nw = (int64_t)cfg.blocks * cfg.W;
+  if (!rc && p->partial_cap < nw * 4) {
+    if (p->d_partial) cudaFree(p->d_partial);
+    p->d_partial = nullptr;
+    p->partial_cap = 0;
+    if (cudaMalloc(&p->d_partial, sizeof(double) * nw * 4) != cudaSuccess) rc = VECCHIA_ENOMEM;
+    else p->partial_cap = nw * 4;
+  }
+  const double* tab = nullptr;
+  if (!rc) rc = get_cov_table(p->family, theta[2], stream, &tab);
+  if (!rc && cudaMemsetAsync(p->d_errloc, 0xFF, sizeof(unsigned long long), stream) != cudaSuccess) rc = VECCHIA_ECUDA;
+  if (!rc) {
+    LikArgs a;
+    a.xy = d_xy;
+    a.yf = d_y;
+    a.nbr = d_nbr;
+    a.self = d_self;
+    a.tab = tab;
+    a.n = n_new;
+    a.m = (int)m;
+    a.family = p->family;
+    a.sigma2 = theta[0];
+    a.beta = theta[1];
+    a.nu = theta[2];
+    a.tau2 = theta[3];
+    a.partial = p->d_partial;
+    a.terms = nullptr;
+    a.errloc = p->d_errloc;
+    a.xyz = d_xyz;
+    a.metric = p->metric;
+    a.radius = p->radius;
+    a.pmean = mean_dev;
+    a.pvar = var_dev;
+    launch_lik(cfg, false, a, stream);
+    if (cudaGetLastError() != cudaSuccess) rc = VECCHIA_ECUDA;
+  }
+  if (!rc && nbr_host)
+    cp(nbr_host, d_nbr, sizeof(int32_t) * n_new * m, cudaMemcpyDeviceToHost);
+  if (cudaStreamSynchronize(stream) != cudaSuccess && !rc) rc = VECCHIA_ECUDA;
+  cudaFree(d_nbr);
+  cudaFree(d_self);
+  cudaFree(d_xy);
+  cudaFree(d_y);
+  cudaFree(d_xyz);
+  p->last_stream = stream;
+  return rc;
 }
 
 // Times every (lanes per location, warps per CTA) shape on the caller's problem and

@@ -226,6 +226,49 @@ struct BestList {
   }
 };
 
+// Exact ring search of one query in one grid level: every point of the level with index
+// below `limit` is a candidate (cell lists ascend in index); rings of cells are added
+// until the m-th best distance is below the distance to the unscanned cells.
+__device__ void ring_search(const KnnArgs& a, const Level& L, double2 q, int64_t limit, BestList& bl, int mi) {
+  const int32_t* cs = a.cell_start + L.cell_off;
+  const int32_t* pidx = a.pt_idx + L.pt_off;
+  const double2* pxy = a.pt_xy + L.pt_off;
+  const int cx = min(L.Gx - 1, max(0, (int)floor((q.x - L.x0) * L.ih)));
+  const int cy = min(L.Gy - 1, max(0, (int)floor((q.y - L.y0) * L.ih)));
+  const double slop = 1e-9 * L.h + 4e-16 * (fabs(L.x0) + fabs(L.y0) + L.h * (L.Gx + L.Gy));
+  for (int R = 0;; ++R) {
+    for (int dy = -R; dy <= R; ++dy) {
+      const int ay = cy + dy;
+      if (ay < 0 || ay >= L.Gy) continue;
+      const bool edge = (dy == -R || dy == R);
+      for (int dx = -R; dx <= R; dx += edge ? 1 : 2 * R) {
+        const int ax = cx + dx;
+        if (ax >= 0 && ax < L.Gx) {
+          const int c = ay * L.Gx + ax;
+          for (int t = cs[c]; t < cs[c + 1]; ++t) {
+            const int j = pidx[t];
+            if (j >= limit) break;  // cell lists ascend in index
+            bl.offer(__double_as_longlong(kd2(q, pxy[t])), j, mi);
+          }
+        }
+        if (R == 0) break;
+      }
+    }
+    const bool all = (cx - R <= 0) && (cy - R <= 0) && (cx + R >= L.Gx - 1) && (cy + R >= L.Gy - 1);
+    if (all) break;
+    if (bl.cnt == mi) {
+      // distance from q to the outside of the scanned square of cells
+      double bd = INFINITY;
+      if (cx - R > 0) bd = fmin(bd, q.x - (L.x0 + (cx - R) * L.h));
+      if (cx + R < L.Gx - 1) bd = fmin(bd, (L.x0 + (cx + R + 1) * L.h) - q.x);
+      if (cy - R > 0) bd = fmin(bd, q.y - (L.y0 + (cy - R) * L.h));
+      if (cy + R < L.Gy - 1) bd = fmin(bd, (L.y0 + (cy + R + 1) * L.h) - q.y);
+      bd -= slop;
+      if (bd > 0.0 && bd * bd * (1.0 - 1e-12) > __longlong_as_double(bl.d[mi - 1])) break;
+    }
+  }
+}
+
 __global__ void knn_kernel(const KnnArgs a) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= a.n) return;
@@ -239,58 +282,33 @@ __global__ void knn_kernel(const KnnArgs a) {
   } else {
     int lv = 0;
     while (lv < a.nlev - 1 && a.levels[lv].N < i) ++lv;
-    const Level L = a.levels[lv];
-    const int32_t* cs = a.cell_start + L.cell_off;
-    const int32_t* pidx = a.pt_idx + L.pt_off;
-    const double2* pxy = a.pt_xy + L.pt_off;
-    const int cx = min(L.Gx - 1, max(0, (int)floor((q.x - L.x0) * L.ih)));
-    const int cy = min(L.Gy - 1, max(0, (int)floor((q.y - L.y0) * L.ih)));
-    const double slop = 1e-9 * L.h + 4e-16 * (fabs(L.x0) + fabs(L.y0) + L.h * (L.Gx + L.Gy));
-    for (int R = 0;; ++R) {
-      for (int dy = -R; dy <= R; ++dy) {
-        const int ay = cy + dy;
-        if (ay < 0 || ay >= L.Gy) continue;
-        const bool edge = (dy == -R || dy == R);
-        for (int dx = -R; dx <= R; dx += edge ? 1 : 2 * R) {
-          const int ax = cx + dx;
-          if (ax >= 0 && ax < L.Gx) {
-            const int c = ay * L.Gx + ax;
-            for (int t = cs[c]; t < cs[c + 1]; ++t) {
-              const int j = pidx[t];
-              if (j >= i) break;  // cell lists ascend in ordered index
-              bl.offer(__double_as_longlong(kd2(q, pxy[t])), j, mi);
-            }
-          }
-          if (R == 0) break;
-        }
-      }
-      const bool all = (cx - R <= 0) && (cy - R <= 0) && (cx + R >= L.Gx - 1) && (cy + R >= L.Gy - 1);
-      if (all) break;
-      if (bl.cnt == mi) {
-        // distance from q to the outside of the scanned square of cells
-        double bd = INFINITY;
-        if (cx - R > 0) bd = fmin(bd, q.x - (L.x0 + (cx - R) * L.h));
-        if (cx + R < L.Gx - 1) bd = fmin(bd, (L.x0 + (cx + R + 1) * L.h) - q.x);
-        if (cy - R > 0) bd = fmin(bd, q.y - (L.y0 + (cy - R) * L.h));
-        if (cy + R < L.Gy - 1) bd = fmin(bd, (L.y0 + (cy + R + 1) * L.h) - q.y);
-        bd -= slop;
-        if (bd > 0.0 && bd * bd * (1.0 - 1e-12) > __longlong_as_double(bl.d[mi - 1])) break;
-      }
-    }
+    ring_search(a, a.levels[lv], q, i, bl, mi);
   }
   int32_t* out = a.nbr + i * m;
   for (int p = 0; p < m; ++p) out[p] = p < bl.cnt ? (int32_t)a.perm[bl.id[p]] : -1;
 }
 
+// Prediction queries: the m nearest of ALL points of the single level (original order,
+// so ties go to the lower original index) for each query point.
+__global__ void knn_query_kernel(const KnnArgs a, const double2* __restrict__ queries, int64_t nq) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= nq) return;
+  BestList bl;
+  bl.cnt = 0;
+  ring_search(a, a.levels[0], queries[k], a.levels[0].N, bl, a.m);
+  int32_t* out = a.nbr + k * a.m;
+  for (int p = 0; p < a.m; ++p) out[p] = p < bl.cnt ? bl.id[p] : -1;
+}
+
 static void build_levels(int64_t n, const double* xyo, std::vector<Level>& lev, std::vector<int32_t>& cs,
-                         std::vector<int32_t>& pidx, std::vector<double>& pxy) {
+                         std::vector<int32_t>& pidx, std::vector<double>& pxy, int64_t first_N = kBrute) {
   double x0 = xyo[0], x1 = xyo[0], y0 = xyo[1], y1 = xyo[1];
   for (int64_t i = 1; i < n; ++i) {
     x0 = std::min(x0, xyo[2 * i]); x1 = std::max(x1, xyo[2 * i]);
     y0 = std::min(y0, xyo[2 * i + 1]); y1 = std::max(y1, xyo[2 * i + 1]);
   }
   const double wx = std::max(x1 - x0, 1e-300), wy = std::max(y1 - y0, 1e-300);
-  int64_t N = kBrute;
+  int64_t N = first_N;
   while (true) {
     const int64_t Nl = std::min<int64_t>(N, n);
     Level L;
@@ -410,11 +428,13 @@ static void sphere_unit_vectors(int64_t n, const double* lonlat, double* xyz) {
 }
 
 struct SphereKnnArgs {
-  const double* __restrict__ xyzo;  // ordered unit vectors, n x 3
+  const double* __restrict__ xyzo;  // candidates: ordered unit vectors, n x 3
   int64_t n;
   int m;
-  const int64_t* __restrict__ perm;  // ordered -> original
-  int32_t* nbr;                      // n x m, ORIGINAL indices
+  const int64_t* __restrict__ perm;  // ordered -> original (nullptr: candidates are in original order)
+  int32_t* nbr;                      // rows x m, ORIGINAL indices
+  const double* __restrict__ queries = nullptr;  // prediction: nq x 3 query unit vectors, all n candidates
+  int64_t nq = 0;
 };
 
 constexpr int kSphereTile = 256;
@@ -427,22 +447,26 @@ constexpr int kSphereTile = 256;
 __global__ void __launch_bounds__(128) knn_sphere_kernel(const SphereKnnArgs a) {
   __shared__ double tx[kSphereTile], ty[kSphereTile], tz[kSphereTile];
   __shared__ float fx[kSphereTile], fy[kSphereTile], fz[kSphereTile];
+  const bool query = a.queries != nullptr;
   const int64_t i0 = (int64_t)blockIdx.x * blockDim.x;
   const int64_t i = i0 + threadIdx.x;
-  const bool live = i < a.n;
+  const bool live = i < (query ? a.nq : a.n);
   const int m = a.m;
-  const int mi = live ? (int)(i < m ? i : m) : 0;
+  const int mi = live ? (query ? m : (int)(i < m ? i : m)) : 0;
+  const int64_t limit = query ? a.n : i;  // candidates j < limit
   BestList bl;
   bl.cnt = 0;
   double qx = 0.0, qy = 0.0, qz = 0.0;
   if (live) {
-    qx = a.xyzo[3 * i];
-    qy = a.xyzo[3 * i + 1];
-    qz = a.xyzo[3 * i + 2];
+    const double* qp = query ? a.queries + 3 * i : a.xyzo + 3 * i;
+    qx = qp[0];
+    qy = qp[1];
+    qz = qp[2];
   }
   const float gx = (float)qx, gy = (float)qy, gz = (float)qz;
   float wf = INFINITY;  // prefilter threshold (stays infinite until the list is full)
-  const int64_t jend = min(a.n, i0 + (int64_t)blockDim.x) - 1;  // largest i in the block, exclusive bound
+  // candidates any thread of the block needs: [0, jend)
+  const int64_t jend = query ? a.n : min(a.n, i0 + (int64_t)blockDim.x) - 1;
   for (int64_t t0 = 0; t0 < jend; t0 += kSphereTile) {
     __syncthreads();
     for (int k = threadIdx.x; k < kSphereTile; k += blockDim.x) {
@@ -459,7 +483,7 @@ __global__ void __launch_bounds__(128) knn_sphere_kernel(const SphereKnnArgs a) 
     }
     __syncthreads();
     if (!live) continue;
-    const int kend = (int)min((int64_t)kSphereTile, i - t0);
+    const int kend = (int)min((int64_t)kSphereTile, limit - t0);
     for (int k = 0; k < kend; ++k) {
       const float ex = fx[k] - gx, ey = fy[k] - gy, ez = fz[k] - gz;
       if (ex * ex + ey * ey + ez * ez > wf) continue;
@@ -478,7 +502,7 @@ __global__ void __launch_bounds__(128) knn_sphere_kernel(const SphereKnnArgs a) 
   }
   if (!live) return;
   int32_t* out = a.nbr + i * m;
-  for (int p = 0; p < m; ++p) out[p] = p < bl.cnt ? (int32_t)a.perm[bl.id[p]] : -1;
+  for (int p = 0; p < m; ++p) out[p] = p < bl.cnt ? (int32_t)(a.perm ? a.perm[bl.id[p]] : bl.id[p]) : -1;
 }
 
 static int knn_sphere_gpu(Plan* p, const double* xyz_host, cudaStream_t stream) {
@@ -512,6 +536,92 @@ static int knn_sphere_gpu(Plan* p, const double* xyz_host, cudaStream_t stream) 
   return rc;
 }
 
+// Conditioning sets of prediction points: the m nearest OBSERVED points of the plan
+// (all of them are candidates; ties to the lower original index), written to d_nbr_new
+// (n_new x m, original indices) on `stream`.  xy_new_host: n_new x 2 (plane) or
+// (longitude, latitude) in degrees (sphere); for the sphere, xyz_new_out receives the
+// query unit vectors (n_new x 3, host).
+int knn_predict(Plan* p, const double* xy_new_host, int64_t n_new, int32_t* d_nbr_new, std::vector<double>* xyz_new_out,
+                cudaStream_t stream) {
+  const int64_t n = p->n;
+  int rc = VECCHIA_OK;
+  if (p->metric == 1) {
+    std::vector<double>& xyzq = *xyz_new_out;
+    xyzq.resize(3 * n_new);
+    sphere_unit_vectors(n_new, xy_new_host, xyzq.data());
+    double* d_q = nullptr;
+    if (cudaMalloc(&d_q, sizeof(double) * 3 * n_new) != cudaSuccess) return VECCHIA_ENOMEM;
+    if (cudaMemcpyAsync(d_q, xyzq.data(), sizeof(double) * 3 * n_new, cudaMemcpyHostToDevice, stream) != cudaSuccess)
+      rc = VECCHIA_ECUDA;
+    if (!rc) {
+      SphereKnnArgs a;
+      a.xyzo = p->d_xyz;  // original order
+      a.n = n;
+      a.m = p->m;
+      a.perm = nullptr;
+      a.nbr = d_nbr_new;
+      a.queries = d_q;
+      a.nq = n_new;
+      knn_sphere_kernel<<<(unsigned)((n_new + 127) / 128), 128, 0, stream>>>(a);
+      if (cudaGetLastError() != cudaSuccess) rc = VECCHIA_ECUDA;
+    }
+    if (!rc && cudaStreamSynchronize(stream) != cudaSuccess) rc = VECCHIA_ECUDA;
+    cudaFree(d_q);
+    return rc;
+  }
+  std::vector<double> xy(2 * n);
+  if (cudaMemcpy(xy.data(), p->d_xy, sizeof(double) * 2 * n, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return VECCHIA_ECUDA;
+  std::vector<Level> lev;
+  std::vector<int32_t> cs, pidx;
+  std::vector<double> pxy;
+  build_levels(n, xy.data(), lev, cs, pidx, pxy, n);  // one level over all points, original order
+  double *d_pxy = nullptr, *d_q = nullptr;
+  int32_t *d_cs = nullptr, *d_pidx = nullptr;
+  Level* d_lev = nullptr;
+  auto alloc = [&](void** ptr, size_t bytes) {
+    if (rc) return;
+    if (cudaMalloc(ptr, std::max<size_t>(bytes, 16)) != cudaSuccess) rc = VECCHIA_ENOMEM;
+  };
+  alloc((void**)&d_pxy, sizeof(double) * pxy.size());
+  alloc((void**)&d_cs, sizeof(int32_t) * cs.size());
+  alloc((void**)&d_pidx, sizeof(int32_t) * pidx.size());
+  alloc((void**)&d_lev, sizeof(Level) * lev.size());
+  alloc((void**)&d_q, sizeof(double) * 2 * n_new);
+  auto up = [&](void* dst, const void* src, size_t bytes) {
+    if (rc) return;
+    if (cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, stream) != cudaSuccess) rc = VECCHIA_ECUDA;
+  };
+  up(d_pxy, pxy.data(), sizeof(double) * pxy.size());
+  up(d_cs, cs.data(), sizeof(int32_t) * cs.size());
+  up(d_pidx, pidx.data(), sizeof(int32_t) * pidx.size());
+  up(d_lev, lev.data(), sizeof(Level) * lev.size());
+  up(d_q, xy_new_host, sizeof(double) * 2 * n_new);
+  if (!rc) {
+    KnnArgs a;
+    a.xyo = nullptr;
+    a.cell_start = d_cs;
+    a.pt_idx = d_pidx;
+    a.pt_xy = reinterpret_cast<const double2*>(d_pxy);
+    a.levels = d_lev;
+    a.nlev = (int)lev.size();
+    a.n = n;
+    a.m = p->m;
+    a.perm = nullptr;
+    a.nbr = d_nbr_new;
+    knn_query_kernel<<<(unsigned)((n_new + 127) / 128), 128, 0, stream>>>(a, reinterpret_cast<const double2*>(d_q),
+                                                                           n_new);
+    if (cudaGetLastError() != cudaSuccess) rc = VECCHIA_ECUDA;
+  }
+  if (!rc && cudaStreamSynchronize(stream) != cudaSuccess) rc = VECCHIA_ECUDA;
+  cudaFree(d_pxy);
+  cudaFree(d_cs);
+  cudaFree(d_pidx);
+  cudaFree(d_lev);
+  cudaFree(d_q);
+  return rc;
+}
+
 static void plan_free(Plan* p) {
   if (!p) return;
   cudaFree(p->d_xyz);
@@ -527,6 +637,8 @@ static void plan_free(Plan* p) {
 
 int launch_loglik(Plan* p, const double* y_dev, const double* theta, bool grad, double* out_dev,
                   double* terms_dev, cudaStream_t stream);
+int predict(Plan* p, const double* xy_new_host, int64_t n_new, const double* y_dev, const double* theta,
+            double* mean_dev, double* var_dev, int32_t* nbr_host, cudaStream_t stream);
 void forget_plan_in_batches(const void* plan);
 int autotune(Plan* p, const double* y_dev, const double* theta, bool grad, int* G_out, int* W_out,
              cudaStream_t stream);
@@ -690,6 +802,11 @@ int vecchia_autotune(vecchia_plan_t plan, const double* y_dev, const double thet
   if (lanes_out) *lanes_out = G;
   if (warps_out) *warps_out = W;
   return VECCHIA_OK;
+}
+
+int vecchia_predict(vecchia_plan_t plan, const double* xy_new_host, int64_t n_new, const double* y_dev,
+                    const double theta[4], double* mean_dev, double* var_dev, int32_t* nbr_host, void* stream) {
+  return vecchia::predict(plan, xy_new_host, n_new, y_dev, theta, mean_dev, var_dev, nbr_host, (cudaStream_t)stream);
 }
 
 int vecchia_last_error_location(vecchia_plan_t plan, int64_t* loc) {

@@ -44,6 +44,7 @@ SIGNATURES = {
     "vecchia_plan_create_sphere": (ctypes.c_int, [_dp, _i64, _i32, ctypes.c_int, ctypes.c_uint64,
                                                   ctypes.POINTER(_i64), ctypes.c_double, _vp, ctypes.POINTER(_vp)]),
     "vecchia_plan_destroy": (None, [_vp]),
+    "vecchia_predict": (ctypes.c_int, [_vp, _dp, _i64, _vp, _dp, _vp, _vp, ctypes.POINTER(_i32), _vp]),
     "vecchia_plan_size": (ctypes.c_int, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i32)]),
     "vecchia_plan_set_kernel": (ctypes.c_int, [_vp, ctypes.c_int]),
     "vecchia_covariance": (ctypes.c_int, [ctypes.c_int, _vp, _i64, _dp, _vp, _vp, _vp]),
@@ -282,6 +283,25 @@ class Batch:
                                           1 if self.want_grad else 0, _vp(out.data_ptr()), _vp(_stream(stream)))
         _check(rc, "vecchia_loglik_batched")
         return out
+
+
+def vecchia_predict(plan: Plan, xy_new, y, theta, with_var: bool = True, return_neighbors: bool = False,
+                    stream=None):
+    """Kriging at new locations from the m nearest observed points of ``plan``:
+    (mean, var) as CUDA float64 tensors (var None unless ``with_var``), plus the
+    conditioning sets (n_new x m original indices) when ``return_neighbors``."""
+    xn = np.ascontiguousarray(np.asarray(xy_new, dtype=np.float64).reshape(-1, 2))
+    k = int(xn.shape[0])
+    y = _dev_f64(y, plan.n, "y")
+    mean = torch.empty(k, dtype=torch.float64, device=y.device)
+    var = torch.empty(k, dtype=torch.float64, device=y.device) if with_var else None
+    nbr = np.empty((k, plan.m), dtype=np.int32) if return_neighbors else None
+    rc = lib().vecchia_predict(plan.handle, xn.ctypes.data_as(_dp), k, _vp(y.data_ptr()), _theta(theta),
+                               _vp(mean.data_ptr()), _vp(var.data_ptr()) if var is not None else None,
+                               nbr.ctypes.data_as(ctypes.POINTER(_i32)) if nbr is not None else None,
+                               _vp(_stream(stream)))
+    _check(rc, "vecchia_predict")
+    return (mean, var, nbr) if return_neighbors else (mean, var)
 
 
 def vecchia_covariance(kernel: int, d: torch.Tensor, theta, with_dbeta: bool = True, stream=None):
