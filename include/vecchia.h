@@ -272,7 +272,10 @@ int vecchia_loglik_noalloc(const double* xy_dev, const double* y_dev, const int3
  * up to 16 rows use 8 lanes, up to 32 rows 16 lanes, larger ones a full warp.  Not in
  * the paper (its batched kernels are library routines).
  *   y_dev, theta : as for vecchia_loglik (theta on the host).
- *   lanes_out, warps_out : host int32 (may be NULL): the chosen shape.
+ *   lanes_out, warps_out : host int32 (may be NULL): the chosen shape.  For m >
+ *                          VECCHIA_MAX_M_WARP (one CTA per location, sized by
+ *                          occupancy) nothing is timed: lanes_out = the CTA's threads,
+ *                          warps_out = its warps.
  * Synchronous (waits on `stream`); must not be called during stream capture.
  * Errors: EINVAL, ENOMEM, ECUDA.
  */

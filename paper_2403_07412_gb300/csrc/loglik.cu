@@ -481,9 +481,12 @@ int autotune(Plan* p, const double* y_dev, const double* theta, bool grad, int* 
              cudaStream_t stream) {
   if (!p || !y_dev || !theta_ok_family(theta, p->family)) return VECCHIA_EINVAL;
   const int K = p->m + 1;
-  if (p->m > kMaxMWarp) {  // one CTA of 4 warps per location: nothing to choose
-    if (G_out) *G_out = 128;
-    if (W_out) *W_out = 4;
+  if (p->m > kMaxMWarp) {  // one CTA per location, sized by occupancy: nothing to time
+    int blocks = 0, threads = 0, smem = 0;
+    const int rc = big_config(K, grad, &blocks, &threads, &smem, p->metric == 1);
+    if (rc) return rc;
+    if (G_out) *G_out = threads;
+    if (W_out) *W_out = threads / 32;
     return VECCHIA_OK;
   }
   int dev = 0;

@@ -80,3 +80,12 @@ def test_sphere_plan_argument_checks_without_gpu(libpath):
     assert L.vecchia_plan_create_sphere(ll, 2, 1, vecchia.ORDER_RANDOM, 0, None, float("inf"), None,
                                         ctypes.byref(out)) == vecchia.EINVAL
 
+
+def test_predict_argument_checks_without_gpu(libpath):
+    from paper_2403_07412_gb300 import vecchia
+
+    L = vecchia.lib()
+    xy = (ctypes.c_double * 2)(0.5, 0.5)
+    th = (ctypes.c_double * 4)(1.0, 0.1, 0.5, 0.0)
+    assert L.vecchia_predict(None, xy, 1, None, th, None, None, None, None) == vecchia.EINVAL
+

@@ -358,6 +358,10 @@ def test_autotune_records_a_shape(V):
     assert abs(after[0] - before[0]) <= W.LOGLIK_RTOL * den[0]
     for k in (1, 2, 3):
         assert abs(after[k] - before[k]) <= W.GRAD_RTOL * den[k]
+    # m beyond the warp kernels: nothing to time, the CTA size chosen by occupancy
+    q = V.Plan(xy[:3000], 100)
+    t, wq = V.vecchia_autotune(q, _dev(y[:3000]), theta, want_grad=False)
+    assert t in (128, 256) and wq == t // 32
 
 
 @pytest.mark.parametrize("alpha", [0.5, 1.0, 1.5, 2.0])
