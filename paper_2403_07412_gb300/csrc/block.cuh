@@ -192,8 +192,8 @@ __device__ __forceinline__ float2 d2f_pair(double x) {
 // relative), in double-float arithmetic on the FP32 pipe: (uh, ul) within about 2^-46
 // of |p_r - p_c|^2 relative, plus 2^-47 of the block's coordinate scale in |p_r - p_c|.
 // A covariance entry needs absolute accuracy, and |drho/du| |du| stays far below the
-// factorisation's own rounding.  (An exact 128-bit fixed-point square costs ~70 integer
-// instructions at half rate; this costs ~41 full-rate FP32 ones.)
+// factorisation's own rounding.  (An exact square of 64-bit integer coordinates costs
+// ~70 integer instructions at half rate; this costs ~41 full-rate FP32 ones.)
 __device__ __forceinline__ void df_diff(float2 a, float2 b, float& h, float& l) {
   float s, e;
   two_sum(a.x, -b.x, s, e);

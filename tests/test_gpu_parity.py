@@ -73,10 +73,11 @@ def test_matern_matches_oracle(V, nu):
     # factors (pow, tgamma, K_nu, ...), the table adds its fit (< 1e-16) and Horner rounding.
     err = np.abs(c - want)
     assert np.all(err <= 4e-15 * sigma2), (err.max(), d[np.argmax(err)])
-    # dC/dbeta carries the FP32 tail of the derivative polynomial: ~1e-9 relative where
-    # the correlation exceeds 1e-3, a few 1e-8 relative where it is below 1e-6.  What the
-    # gradient needs is an absolute error small against the largest |dC/dbeta|, so the
-    # bound is 2e-9 relative plus 1e-10 of the largest magnitude.
+    # dC/dbeta is a double-float evaluation whose high-order tail (c5..c8) is plain FP32:
+    # ~1e-14 relative where the correlation is not small, up to ~1e-8 relative where
+    # |dC/dbeta| is tiny against its largest value.  What the gradient needs is an
+    # absolute error small against the largest |dC/dbeta|, so the bound is 2e-9
+    # relative plus 1e-10 of the largest magnitude.
     ratio = np.abs(dc - wantd) / (2e-9 * np.abs(wantd) + 1e-10 * np.abs(wantd).max())
     k = int(np.argmax(ratio))
     assert ratio[k] <= 1.0, (ratio[k], d[k] / beta, dc[k], wantd[k])

@@ -125,3 +125,23 @@ def test_sphere_plan_rejections(V):
     b = V.Batch([p], [_dev(np.zeros(200))], 1, want_grad=False)
     with pytest.raises(V.VecchiaError):
         b.run(_dev(np.array([[[1.0, 50.0, 0.5, 0.0]]])))
+
+
+def test_sphere_gradient_central_differences(V):
+    # dl/d(sigma2, beta, tau2) through the asin series against central differences of
+    # the GPU forward (h = 1e-6 relative, as for the planar path).
+    n, m = 4000, 25
+    theta = np.array([1.1, 45.0, 0.5, 0.03])
+    ll = datagen.sphere_locations(n, 250)
+    y = _field(ll, tuple(theta), 251)
+    p = V.Plan(ll, m, order=V.ORDER_RANDOM, seed=4, radius=R_EARTH)
+    yd = _dev(y)
+    g = V.vecchia_loglik_grad(p, yd, tuple(theta)).cpu().numpy()
+    for k, idx in ((1, 0), (2, 1), (3, 3)):
+        h = 1e-6 * theta[idx]
+        tp, tm = theta.copy(), theta.copy()
+        tp[idx] += h
+        tm[idx] -= h
+        fd = (V.vecchia_loglik(p, yd, tuple(tp)).item() - V.vecchia_loglik(p, yd, tuple(tm)).item()) / (2 * h)
+        assert abs(g[k] - fd) <= 1e-6 * abs(fd) + 1e-9 * abs(g[0]), (k, g[k], fd)
+
