@@ -47,12 +47,18 @@ def la_flops(n: int, m: int, grad: bool) -> float:
 
 
 def kernel_source_hash() -> str:
+    """Hash of the CUDA sources with comments and blank space removed, so that the DRAM
+    counters in profiles/traffic.json stay attached to the code they were taken on."""
     import glob
     import hashlib
+    import re
 
     h = hashlib.sha256()
     for f in sorted(glob.glob(os.path.join(ROOT, "paper_2403_07412_gb300", "csrc", "*.cu*"))):
-        h.update(open(f, "rb").read())
+        src = open(f, encoding="utf-8").read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        h.update(re.sub(r"\s+", " ", src).strip().encode())
     return h.hexdigest()[:16]
 
 
