@@ -264,13 +264,14 @@ int vecchia_loglik_noalloc(const double* xy_dev, const double* y_dev, const int3
 
 /*
  * vecchia_autotune — picks the launch shape of the likelihood kernels for this plan's
- * block size (m + 1) by timing: lanes per location (8, 16 or 32; 32/lanes locations share
- * a warp) and warps per CTA.  Each candidate is timed on the caller's own problem (two
+ * block size (m + 1) by timing: lanes per location (4, 8, 16 or 32; 32/lanes locations
+ * share a warp; 4 lanes take blocks of up to 16 rows, 8 lanes up to 32) and warps per CTA.  Each candidate is timed on the caller's own problem (two
  * timed launches after one warm-up; the fastest wins) and recorded, process-wide, for
  * every later call with the same block size and kind (want_grad) on this device,
  * including the batched call's layouts created afterwards.  Without tuning, blocks of
- * up to 16 rows use 8 lanes, up to 32 rows 16 lanes, larger ones a full warp.  Not in
- * the paper (its batched kernels are library routines).
+ * up to 16 rows use 4 lanes, up to 32 rows 8, up to 48 rows 16 (forward) or 32
+ * (gradient), larger ones a full warp.
+ * Not in the paper (its batched kernels are library routines).
  *   y_dev, theta : as for vecchia_loglik (theta on the host).
  *   lanes_out, warps_out : host int32 (may be NULL): the chosen shape.  For m >
  *                          VECCHIA_MAX_M_WARP (one CTA per location, sized by

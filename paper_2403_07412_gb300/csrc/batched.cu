@@ -141,7 +141,8 @@ __global__ void __launch_bounds__(384) vecchia_batched_kernel(const BatchArgs a)
     const MaternConst mc = load_matern_const(tab);
     ThetaConst tc;
     tc.set(s2, beta, t2, kFamilyMatern, nu);
-    if (fd.lanes == 8) run_item<GRAD, 8>(fd, tile, smem, a, base, tab, mc, tc, out, lane);
+    if (fd.lanes == 4) run_item<GRAD, 4>(fd, tile, smem, a, base, tab, mc, tc, out, lane);
+    else if (fd.lanes == 8) run_item<GRAD, 8>(fd, tile, smem, a, base, tab, mc, tc, out, lane);
     else if (fd.lanes == 16) run_item<GRAD, 16>(fd, tile, smem, a, base, tab, mc, tc, out, lane);
     else run_item<GRAD, 32>(fd, tile, smem, a, base, tab, mc, tc, out, lane);
     __syncwarp();

@@ -312,7 +312,8 @@ __device__ __forceinline__ void process_location(int64_t i, bool active, const F
                                                  const double* __restrict__ tab, const MaternConst& mc,
                                                  const ThetaConst& tc, Accum& acc, bool terms_mode,
                                                  double* terms, unsigned long long* errloc, int sub) {
-  constexpr int NSG = (kMaxMWarp + G) / G;  // neighbour slots per lane (m <= kMaxMWarp)
+  constexpr int KCAP = max_k_for_lanes(G);
+  constexpr int NSG = (KCAP - 1 + G - 1) / G;  // neighbour slots per lane (m <= KCAP - 1)
   const int m = F.m;
   const int K = m + 1;
   double* __restrict__ A = W.A;
@@ -471,7 +472,7 @@ __device__ __forceinline__ void process_location(int64_t i, bool active, const F
   // ---- adjoint: w = L_J^{-T} (row m of L), alpha~ = L_J^{-T} (row K of L)
   double* __restrict__ WH = W.WH;
   double* __restrict__ GV = W.GV;
-  constexpr int NS = (kMaxMWarp + G - 1) / G;  // slots of the K-1 <= kMaxMWarp neighbour entries
+  constexpr int NS = (KCAP - 1 + G - 1) / G;  // slots of the K-1 <= KCAP-1 neighbour entries
   double w[NS], bv[NS];
 #pragma unroll
   for (int t = 0; t < NS; ++t) {

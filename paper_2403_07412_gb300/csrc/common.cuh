@@ -28,6 +28,10 @@ constexpr size_t kTableBytes = (size_t)16 * kIntWords * kNInt + sizeof(double) *
 // Largest conditioning sets: overall (CTA-per-location kernel) and for the warp kernels.
 constexpr int kMaxM = VECCHIA_MAX_M;
 constexpr int kMaxMWarp = VECCHIA_MAX_M_WARP;
+// Largest block (K = m + 1 rows) a group of G lanes per location handles: narrow groups
+// keep at most four neighbour slots per lane, so their per-lane register arrays (and the
+// selects that index them) stay short.
+__host__ __device__ constexpr int max_k_for_lanes(int G) { return G == 4 ? 16 : (G == 8 ? 32 : kMaxMWarp + 1); }
 
 // Covariance families (VECCHIA_KERNEL_*): Matérn, Eq. (2); power exponential, Eq. (3).
 constexpr int kFamilyMatern = 0;

@@ -158,6 +158,7 @@ struct LaunchCfg {
 
 template <bool GRAD, bool SPHERE>
 void* kernel_ptr(int G) {
+  if (G == 4) return reinterpret_cast<void*>(vecchia_lik_kernel<GRAD, 4, SPHERE>);
   if (G == 8) return reinterpret_cast<void*>(vecchia_lik_kernel<GRAD, 8, SPHERE>);
   if (G == 16) return reinterpret_cast<void*>(vecchia_lik_kernel<GRAD, 16, SPHERE>);
   return reinterpret_cast<void*>(vecchia_lik_kernel<GRAD, 32, SPHERE>);
@@ -168,8 +169,15 @@ void* lik_kernel(bool grad, int G, bool sphere) {
   return sphere ? kernel_ptr<false, true>(G) : kernel_ptr<false, false>(G);
 }
 
-// Lanes per location chosen when no tuning result exists: small blocks share a warp.
-int default_lanes(int K) { return K <= 16 ? 8 : (K <= 32 ? 16 : 32); }
+// Lanes per location chosen when no tuning result exists: small blocks share a warp.  The
+// break points are the fastest measured shapes on GB300 at n = 1e6 (m = 15, 20, 25, 31,
+// 45, 60); the adjoint favours wider groups a little earlier than the forward pass.
+int default_lanes(int K, bool grad) {
+  if (K <= 16) return 4;
+  if (K <= 32) return 8;
+  if (K <= 48) return grad ? 32 : 16;
+  return 32;
+}
 
 // Tuning results, per (device, K, grad): lanes per location and warps per CTA.
 struct Tuned {
@@ -203,6 +211,7 @@ void set_tuned(int dev, int K, bool grad, int G, int W) {
 // Launch shape for lanes-per-location G: W (forced_W > 0, else the value giving the most
 // resident warps per SM, ties to the larger CTA) and a persistent grid of one wave.
 int shape_for(int K, bool grad, int G, int forced_W, LaunchCfg* cfg, bool sphere = false) {
+  if (K > max_k_for_lanes(G)) return VECCHIA_EINVAL;  // narrow groups hold small blocks only
   int dev = 0, sms = 0, smem_optin = 0;
   VECCHIA_CUDA_TRY(cudaGetDevice(&dev));
   VECCHIA_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -237,25 +246,28 @@ int shape_for(int K, bool grad, int G, int forced_W, LaunchCfg* cfg, bool sphere
 int pick_config(int K, bool grad, LaunchCfg* cfg, bool sphere = false) {
   int dev = 0;
   VECCHIA_CUDA_TRY(cudaGetDevice(&dev));
-  int G = default_lanes(K), W = 0;
+  int G = default_lanes(K, grad), W = 0;
   tuned_for(dev, K, grad, &G, &W);
   if (sphere) W = 0;  // the tuned CTA size was sized for planar blocks
   if (const char* e = getenv("VECCHIA_LANES_PER_LOCATION")) {
     const int v = atoi(e);
-    if (v == 8 || v == 16 || v == 32) G = v;
+    if (v == 4 || v == 8 || v == 16 || v == 32) G = v;
   }
   if (const char* e = getenv("VECCHIA_WARPS_PER_CTA")) W = atoi(e);
+  while (K > max_k_for_lanes(G)) G *= 2;
   return shape_for(K, grad, G, W, cfg, sphere);
 }
 
 template <bool SPHERE>
 void launch_lik_m(const LaunchCfg& cfg, bool grad, const LikArgs& a, cudaStream_t stream) {
   if (grad) {
-    if (cfg.G == 8) vecchia_lik_kernel<true, 8, SPHERE><<<cfg.blocks, cfg.W * 32, cfg.smem, stream>>>(a);
+    if (cfg.G == 4) vecchia_lik_kernel<true, 4, SPHERE><<<cfg.blocks, cfg.W * 32, cfg.smem, stream>>>(a);
+    else if (cfg.G == 8) vecchia_lik_kernel<true, 8, SPHERE><<<cfg.blocks, cfg.W * 32, cfg.smem, stream>>>(a);
     else if (cfg.G == 16) vecchia_lik_kernel<true, 16, SPHERE><<<cfg.blocks, cfg.W * 32, cfg.smem, stream>>>(a);
     else vecchia_lik_kernel<true, 32, SPHERE><<<cfg.blocks, cfg.W * 32, cfg.smem, stream>>>(a);
   } else {
-    if (cfg.G == 8) vecchia_lik_kernel<false, 8, SPHERE><<<cfg.blocks, cfg.W * 32, cfg.smem, stream>>>(a);
+    if (cfg.G == 4) vecchia_lik_kernel<false, 4, SPHERE><<<cfg.blocks, cfg.W * 32, cfg.smem, stream>>>(a);
+    else if (cfg.G == 8) vecchia_lik_kernel<false, 8, SPHERE><<<cfg.blocks, cfg.W * 32, cfg.smem, stream>>>(a);
     else if (cfg.G == 16) vecchia_lik_kernel<false, 16, SPHERE><<<cfg.blocks, cfg.W * 32, cfg.smem, stream>>>(a);
     else vecchia_lik_kernel<false, 32, SPHERE><<<cfg.blocks, cfg.W * 32, cfg.smem, stream>>>(a);
   }
@@ -270,8 +282,8 @@ void launch_lik(const LaunchCfg& cfg, bool grad, const LikArgs& a, cudaStream_t 
 // Lanes per location for block size K: the tuned value if any, else the default.
 int lanes_for(int K, bool grad) {
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return default_lanes(K);
-  int G = default_lanes(K), W = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return default_lanes(K, grad);
+  int G = default_lanes(K, grad), W = 0;
   tuned_for(dev, K, grad, &G, &W);
   return G;
 }
@@ -497,8 +509,9 @@ int autotune(Plan* p, const double* y_dev, const double* theta, bool grad, int* 
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   float best = 1e30f;
-  int bestG = default_lanes(K), bestW = 0, rc = VECCHIA_OK;
-  for (int G : {8, 16, 32}) {
+  int bestG = default_lanes(K, grad), bestW = 0, rc = VECCHIA_OK;
+  for (int G : {4, 8, 16, 32}) {
+    if (K > max_k_for_lanes(G)) continue;
     for (int W : {12, 11, 10, 9, 8, 6, 4}) {
       LaunchCfg cfg;
       if (shape_for(K, grad, G, W, &cfg, p->metric == 1) != VECCHIA_OK) continue;
