@@ -197,6 +197,19 @@ int vecchia_covariance(int kernel, const double* d_dev, int64_t count, const dou
                        double* dcdbeta_dev, void* stream);
 
 /*
+ * vecchia_pivot_reciprocal — the reciprocal the likelihood kernels take of each LDL^T pivot
+ * (the 1/d_j that scales column j), exposed so its accuracy can be checked.  It uses no
+ * FP64 instruction: an FP32 seed, an exact 32-bit integer residual and a second-order
+ * correction in 64-bit fixed point; the result is within about half an ulp of 1/d.
+ *   d_dev   : count doubles on the device.
+ *   out_dev : count doubles on the device: 1/d for d in [2^-1022, 2^1022), NaN otherwise
+ *             (the likelihood kernels report a pivot outside that range as a block that
+ *             is not positive definite).
+ * Asynchronous on `stream`.  Errors: EINVAL (count < 0, or NULL buffers), ECUDA.
+ */
+int vecchia_pivot_reciprocal(const double* d_dev, int64_t count, double* out_dev, void* stream);
+
+/*
  * vecchia_batched_prepare — builds the covariance tables the batched call may use, one per
  * smoothness value nus[0..nnu-1] (each > 0 and finite, 1 <= nnu <= 8), on the current
  * device, replacing the previously prepared set.  Synchronises `stream` before and after

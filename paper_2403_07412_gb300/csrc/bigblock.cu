@@ -157,8 +157,8 @@ __global__ void __launch_bounds__(kCtaThreadsMax) vecchia_big_kernel(const BigAr
     for (int j = 0; j < K - 1; ++j) {
       const int oj = tri_off(K, j);
       const double d = A[oj];
-      if (!positive_finite(d)) { ok = false; break; }  // uniform over the CTA
-      const double inv = rcp_newton(d);
+      if (!pivot_in_range(d)) { ok = false; break; }  // uniform over the CTA
+      const double inv = rcp_fixed(d);
       for (int r = j + 1 + tid; r <= K; r += NTH) {
         const double tv = A[oj + r - j];
         TV[r] = tv;

@@ -388,8 +388,8 @@ __device__ __forceinline__ void process_location(int64_t i, bool active, const F
   for (int j = 0; j < K - 1; ++j) {
     const int oj = tri_off(K, j);
     const double d = A[oj];
-    ok = ok && positive_finite(d);  // a failed block runs on (values unused) to stay in step
-    const double inv = rcp_newton(d);
+    ok = ok && pivot_in_range(d);  // a failed block runs on (values unused) to stay in step
+    const double inv = rcp_fixed(d);
     for (int r = j + 1 + sub; r <= K; r += G) {
       const double tv = A[oj + r - j];
       TV[r] = tv;

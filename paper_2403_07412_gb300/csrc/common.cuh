@@ -73,6 +73,52 @@ __device__ __forceinline__ double rcp_newton(double d) {
   return fma(y, e2, y);
 }
 
+// Reciprocal of a pivot with no FP64 instruction (the FP64 pipe is the bottleneck; the
+// integer and FP32 pipes are idle most of the time).  For normal d in [2^-1022, 2^1022)
+// with mantissa m in [1, 2):
+//  1. y0 = 1/m_hi in FP32 (m_hi = m truncated to 24 bits), as a 32-bit fixed-point Y0 =
+//     y0 2^32; |1 - m y0| < 2^-21.
+//  2. The residual R = 2^84 - M Y0 (M = m 2^52 the 53-bit integer mantissa) is exact in
+//     64-bit wrap-around arithmetic, since |R| < 2^63: R = e 2^84 with e = 1 - m y0.
+//  3. 1/m = y0 / (1 - e) = y0 (1 + e + e^2 + ...); |e|^3 < 2^-63, so Z = 2^62 y0 (1 + e +
+//     e^2) in fixed point is within a few units of 2^62/m, i.e. far below one unit in the
+//     53rd bit.
+//  4. The double is assembled from Z (rounded to 53 bits) and the exponent; a mantissa of
+//     exactly 1 gives a power of two.
+// Other inputs (zero, subnormal, >= 2^1022, negative, non-finite) give an unspecified
+// finite-or-not value: callers reject them first with pivot_in_range.
+__device__ __forceinline__ double rcp_fixed(double d) {
+  const unsigned long long D = (unsigned long long)__double_as_longlong(d);
+  const unsigned E = (unsigned)(D >> 52) & 0x7FFu;
+  const unsigned hi = (unsigned)(D >> 32), lo = (unsigned)D;
+  const unsigned Mhi = (hi & 0xFFFFFu) | 0x100000u;  // M = Mhi 2^32 + lo
+  const float mh = __uint_as_float(0x3F800000u | ((hi & 0xFFFFFu) << 3) | (lo >> 29));
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(mh));
+  const unsigned rb = __float_as_uint(r);  // r in [1/2, 1]: exponent field 126 or 127
+  const unsigned long long Yw = (unsigned long long)((rb & 0x7FFFFFu) | 0x800000u) << ((rb >> 23) - 118u);
+  const unsigned Y0 = Yw > 0xFFFFFFFFull ? 0xFFFFFFFFu : (unsigned)Yw;
+  const unsigned long long P = (unsigned long long)lo * Y0 + ((unsigned long long)(Mhi * Y0) << 32);
+  const long long R = -(long long)P;  // e 2^84
+  const int Rh = (int)(R >> 32);
+  const unsigned Rl = (unsigned)R;
+  long long c1 = ((long long)Y0 * Rh) >> 22;  // Y0 e 2^30, first order
+  c1 += (long long)(((unsigned long long)Y0 * Rl) >> 54);
+  const long long c2 = ((long long)(int)(c1 >> 10) * Rh) >> 42;  // second order
+  const long long Z = ((long long)Y0 << 30) + c1 + c2;        // 2^62 / m, in (2^61, 2^62)
+  const unsigned long long out = (D & 0xFFFFFFFFFFFFFull) == 0ull
+                                     ? (unsigned long long)(2046u - E) << 52
+                                     : ((unsigned long long)(2044u - E) << 52) + (unsigned long long)((Z + 256) >> 9);
+  return __longlong_as_double((long long)out);
+}
+
+// True iff d is a positive normal double below 2^1022 (biased exponent in [1, 2044]),
+// the domain of rcp_fixed; decided on the bit pattern.
+__device__ __forceinline__ bool pivot_in_range(double d) {
+  const long long b = __double_as_longlong(d);
+  return b >= 0x0010000000000000LL && b < 0x7FD0000000000000LL;
+}
+
 // True iff d is a positive finite double, decided on the bit pattern (no FP64 op).
 __device__ __forceinline__ bool positive_finite(double d) {
   const long long b = __double_as_longlong(d);

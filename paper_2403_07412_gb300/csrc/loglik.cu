@@ -544,7 +544,27 @@ int autotune(Plan* p, const double* y_dev, const double* theta, bool grad, int* 
   return VECCHIA_OK;
 }
 
+// ------------------------------------------------------------------ vecchia_pivot_reciprocal
+// The pivot reciprocal on its own: NaN outside its domain.
+__global__ void pivot_reciprocal_kernel(const double* __restrict__ d, int64_t count, double* __restrict__ out) {
+  const double nan = __longlong_as_double(0x7FF8000000000000LL);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = d[i];
+    out[i] = pivot_in_range(v) ? rcp_fixed(v) : nan;
+  }
+}
+
 }  // namespace vecchia
+
+extern "C" int vecchia_pivot_reciprocal(const double* d_dev, int64_t count, double* out_dev, void* stream) {
+  if (count < 0 || (count > 0 && (!d_dev || !out_dev))) return VECCHIA_EINVAL;
+  if (count == 0) return VECCHIA_OK;
+  const int64_t blocks = std::min<int64_t>((count + 255) / 256, 4096);
+  vecchia::pivot_reciprocal_kernel<<<(int)blocks, 256, 0, (cudaStream_t)stream>>>(d_dev, count, out_dev);
+  VECCHIA_CUDA_TRY(cudaGetLastError());
+  return VECCHIA_OK;
+}
 
 // ------------------------------------------------------------------ allocation-free entry
 // Scratch for vecchia_loglik_noalloc: per-warp partial sums for at most

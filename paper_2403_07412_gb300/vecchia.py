@@ -6,7 +6,8 @@ absence is an error: there is no CPU fallback.
 
 The entry points keep the C names: :func:`vecchia_plan_create` (wrapped by
 :class:`Plan`), :func:`vecchia_loglik`, :func:`vecchia_loglik_grad`,
-:func:`vecchia_loglik_terms`, :func:`vecchia_matern`, :func:`vecchia_fp64_peak`,
+:func:`vecchia_loglik_terms`, :func:`vecchia_matern`, :func:`vecchia_pivot_reciprocal`,
+:func:`vecchia_fp64_peak`,
 :func:`vecchia_batched_prepare` and :class:`Batch` (vecchia_loglik_batched),
 :func:`vecchia_loglik_noalloc`;
 :class:`VecchiaLogLik` is the ``torch.autograd.Function`` over theta.
@@ -54,6 +55,7 @@ SIGNATURES = {
     "vecchia_loglik_grad": (ctypes.c_int, [_vp, _vp, _dp, _vp, _vp]),
     "vecchia_loglik_terms": (ctypes.c_int, [_vp, _vp, _dp, ctypes.c_int, _vp, _vp]),
     "vecchia_matern": (ctypes.c_int, [_vp, _i64, _dp, _vp, _vp, _vp]),
+    "vecchia_pivot_reciprocal": (ctypes.c_int, [_vp, _i64, _vp, _vp]),
     "vecchia_last_error_location": (ctypes.c_int, [_vp, ctypes.POINTER(_i64)]),
     "vecchia_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "vecchia_fp64_peak": (ctypes.c_int, [_dp, _vp]),
@@ -221,6 +223,15 @@ def vecchia_matern(d: torch.Tensor, theta, with_dbeta: bool = True, stream=None)
                               _vp(dc.data_ptr()) if dc is not None else None, _vp(_stream(stream)))
     _check(rc, "vecchia_matern")
     return (c, dc) if with_dbeta else c
+
+
+def vecchia_pivot_reciprocal(d: torch.Tensor, stream=None) -> torch.Tensor:
+    """The LDL^T pivot reciprocal of the likelihood kernels: 1/d, NaN outside [2^-1022, 2^1022)."""
+    d = _dev_f64(d, d.numel(), "d")
+    out = torch.empty_like(d)
+    rc = lib().vecchia_pivot_reciprocal(_vp(d.data_ptr()), d.numel(), _vp(out.data_ptr()), _vp(_stream(stream)))
+    _check(rc, "vecchia_pivot_reciprocal")
+    return out
 
 
 def vecchia_loglik_noalloc(xy: torch.Tensor, y: torch.Tensor, nbr: torch.Tensor, self_idx: torch.Tensor,

@@ -59,6 +59,10 @@ def test_strerror_and_argument_checks_without_gpu(libpath):
     th = (ctypes.c_double * 4)(1.0, -0.1, 0.5, 0.0)
     assert L.vecchia_matern(None, 1, th, None, None, None) == vecchia.EINVAL
     assert L.vecchia_loglik(None, None, th, None, None) == vecchia.EINVAL
+    L.vecchia_pivot_reciprocal.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]
+    assert L.vecchia_pivot_reciprocal(None, -1, None, None) == vecchia.EINVAL
+    assert L.vecchia_pivot_reciprocal(None, 3, None, None) == vecchia.EINVAL
+    assert L.vecchia_pivot_reciprocal(None, 0, None, None) == vecchia.OK
 
 
 def test_sphere_plan_argument_checks_without_gpu(libpath):
