@@ -188,6 +188,31 @@ __device__ __forceinline__ float2 d2f_pair(double x) {
   return make_float2(hi, __uint_as_float(__float_as_uint(lo) | sign));
 }
 
+// x as a float pair (hi: x's leading 24 bits, lo: the next 24), by integer operations
+// only; |x| below 2^-100 gives (0, 0).  For values of moderate exponent (factor entries).
+__device__ __forceinline__ float2 d2f_trunc(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7FF) - 1023;
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const float hi = __uint_as_float(sign | ((unsigned)(e + 127) << 23) | (unsigned)((b >> 29) & 0x7FFFFFu));
+  const float lo = fscale(u24_float((unsigned)(b >> 5) & 0xFFFFFFu), e - 23);
+  const bool z = e < -100;
+  return make_float2(z ? 0.0f : hi, z ? 0.0f : __uint_as_float(__float_as_uint(lo) | sign));
+}
+
+// (h, l) -= (a.x + a.y)(b.x + b.y) in double-float arithmetic (about 2^-46 relative).
+__device__ __forceinline__ void df_fms(float& h, float& l, float2 a, float2 b) {
+  const float p = __fmul_rn(a.x, b.x);
+  float pe = fmaf(a.x, b.x, -p);
+  pe = fmaf(a.x, b.y, pe);
+  pe = fmaf(a.y, b.x, pe);
+  float s, e;
+  two_sum(h, -p, s, e);
+  e = __fadd_rn(e, __fsub_rn(l, pe));
+  h = __fadd_rn(s, e);
+  l = __fsub_rn(e, __fsub_rn(h, s));
+}
+
 // Squared distance of two block points held as float pairs (x = hi + lo, about 2^-48
 // relative), in double-float arithmetic on the FP32 pipe: (uh, ul) within about 2^-46
 // of |p_r - p_c|^2 relative, plus 2^-47 of the block's coordinate scale in |p_r - p_c|.
@@ -393,7 +418,13 @@ __device__ __forceinline__ void process_location(int64_t i, bool active, const F
     for (int r = j + 1 + sub; r <= K; r += G) {
       const double tv = A[oj + r - j];
       TV[r] = tv;
-      A[oj + r - j] = tv * inv;
+      // full-warp groups: integer product (no wait behind other warps' FP64 work on the
+      // column step's serial path); narrow groups amortise one DMUL over 32/G locations
+      if constexpr (G == 32) {
+        A[oj + r - j] = mul_by_positive(tv, inv);
+      } else {
+        A[oj + r - j] = tv * inv;
+      }
     }
     __syncwarp();
     // Trailing update of the prefix [1, oj).  Full batches of eight slots per lane are
@@ -473,38 +504,46 @@ __device__ __forceinline__ void process_location(int64_t i, bool active, const F
   double* __restrict__ WH = W.WH;
   double* __restrict__ GV = W.GV;
   constexpr int NS = (KCAP - 1 + G - 1) / G;  // slots of the K-1 <= KCAP-1 neighbour entries
-  double w[NS], bv[NS];
+  // The two unit backward solves run in double-float arithmetic on the FP32 pipe: each
+  // step of their serial chain would otherwise wait behind the other warps' FP64 work.
+  float2 wf[NS], bf[NS];
 #pragma unroll
   for (int t = 0; t < NS; ++t) {
     const int c = sub + G * t;
-    w[t] = 0.0;
-    bv[t] = 0.0;
+    wf[t] = make_float2(0.0f, 0.0f);
+    bf[t] = make_float2(0.0f, 0.0f);
     if (c < K - 1) {
       const int o = tri_off(K, c);
-      w[t] = A[o + m - c];
-      bv[t] = A[o + K - c];
+      wf[t] = d2f_trunc(A[o + m - c]);
+      bf[t] = d2f_trunc(A[o + K - c]);
     }
   }
   for (int c = K - 2; c >= 1; --c) {
     const int src = c % G, sl = c / G;
-    double wsel = w[0], bsel = bv[0];
+    float2 wsel = wf[0], bsel = bf[0];
 #pragma unroll
     for (int t = 1; t < NS; ++t)
       if (sl == t) {
-        wsel = w[t];
-        bsel = bv[t];
+        wsel = wf[t];
+        bsel = bf[t];
       }
-    const double wc = __shfl_sync(0xffffffffu, wsel, src, G);
-    const double bc = __shfl_sync(0xffffffffu, bsel, src, G);
+    const float2 wc = make_float2(__shfl_sync(0xffffffffu, wsel.x, src, G), __shfl_sync(0xffffffffu, wsel.y, src, G));
+    const float2 bc = make_float2(__shfl_sync(0xffffffffu, bsel.x, src, G), __shfl_sync(0xffffffffu, bsel.y, src, G));
 #pragma unroll
     for (int t = 0; t < NS; ++t) {
       const int cc = sub + G * t;
       if (cc < c) {
-        const double l = A[tri_off(K, cc) + c - cc];
-        w[t] = fma(-l, wc, w[t]);
-        bv[t] = fma(-l, bc, bv[t]);
+        const float2 l = d2f_trunc(A[tri_off(K, cc) + c - cc]);
+        df_fms(wf[t].x, wf[t].y, l, wc);
+        df_fms(bf[t].x, bf[t].y, l, bc);
       }
     }
+  }
+  double w[NS], bv[NS];
+#pragma unroll
+  for (int t = 0; t < NS; ++t) {
+    w[t] = f2d_scaled(wf[t].x, 0) + f2d_scaled(wf[t].y, 0);
+    bv[t] = f2d_scaled(bf[t].x, 0) + f2d_scaled(bf[t].y, 0);
   }
   const double rs = rr * inv_s;
   const double cb = 0.5 * (rs * rs - inv_s);

@@ -112,6 +112,34 @@ __device__ __forceinline__ double rcp_fixed(double d) {
   return __longlong_as_double((long long)out);
 }
 
+// a b for b a positive normal double (a pivot reciprocal), by integer arithmetic with
+// round-to-nearest-even: equal to the FP64 product whenever that is normal.  The 106-bit
+// mantissa product is formed from 32-bit limbs; a zero or subnormal a, or a product
+// below the normal range, gives a signed zero, and one above it an infinity.
+__device__ __forceinline__ double mul_by_positive(double a, double b) {
+  const unsigned long long A = (unsigned long long)__double_as_longlong(a);
+  const unsigned long long B = (unsigned long long)__double_as_longlong(b);
+  const unsigned long long sgn = A & 0x8000000000000000ull;
+  const int ea = (int)((A >> 52) & 0x7FFu), eb = (int)((B >> 52) & 0x7FFu);
+  const unsigned ah = ((unsigned)(A >> 32) & 0xFFFFFu) | 0x100000u, al = (unsigned)A;
+  const unsigned bh = ((unsigned)(B >> 32) & 0xFFFFFu) | 0x100000u, bl = (unsigned)B;
+  const unsigned long long lo = (unsigned long long)al * bl;
+  const unsigned long long mid = (unsigned long long)ah * bl + (unsigned long long)al * bh;  // < 2^54
+  const unsigned long long plo = lo + (mid << 32);
+  const unsigned long long phi = (unsigned long long)ah * bh + (mid >> 32) + (plo < lo ? 1ull : 0ull);
+  const int top = (int)(phi >> 41) & 1;  // product in [2^105, 2^106)
+  const int sh = 52 + top;
+  unsigned long long m = (phi << (64 - sh)) | (plo >> sh);
+  const unsigned long long rnd = (plo >> (sh - 1)) & 1ull;
+  const unsigned long long sticky = (plo & ((1ull << (sh - 1)) - 1ull)) != 0ull ? 1ull : 0ull;
+  m += rnd & (sticky | (m & 1ull));  // a carry out of 53 bits moves into the exponent field
+  const int e = ea + eb - 1023 + top;
+  unsigned long long r = sgn + ((unsigned long long)(e - 1) << 52) + m;
+  r = (ea == 0 || e <= 0) ? sgn : r;
+  r = e >= 2047 ? (sgn | 0x7FF0000000000000ull) : r;
+  return __longlong_as_double((long long)r);
+}
+
 // True iff d is a positive normal double below 2^1022 (biased exponent in [1, 2044]),
 // the domain of rcp_fixed; decided on the bit pattern.
 __device__ __forceinline__ bool pivot_in_range(double d) {
