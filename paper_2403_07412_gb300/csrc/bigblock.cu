@@ -217,39 +217,47 @@ __global__ void __launch_bounds__(kCtaThreadsMax) vecchia_big_kernel(const BigAr
     const double rsa = rs * tc.inv_sigma2;
     double pT = 0.0;
     if (wid == 0 && good) {
+      // double-float solves on the FP32 pipe, as in the warp kernels: each step of the
+      // serial chain would otherwise wait behind the other CTA's FP64 work
       constexpr int NS = (kMaxM + 31) / 32;
-      double w[NS], bv[NS];
+      float2 wf[NS], bf[NS];
 #pragma unroll
       for (int t = 0; t < NS; ++t) {
         const int c = lane + 32 * t;
-        w[t] = 0.0;
-        bv[t] = 0.0;
+        wf[t] = make_float2(0.0f, 0.0f);
+        bf[t] = make_float2(0.0f, 0.0f);
         if (c < K - 1) {
           const int o = tri_off(K, c);
-          w[t] = A[o + m - c];
-          bv[t] = A[o + K - c];
+          wf[t] = d2f_trunc(A[o + m - c]);
+          bf[t] = d2f_trunc(A[o + K - c]);
         }
       }
       for (int c = K - 2; c >= 1; --c) {
         const int src = c & 31, sl = c >> 5;
-        double wsel = w[0], bsel = bv[0];
+        float2 wsel = wf[0], bsel = bf[0];
 #pragma unroll
         for (int t = 1; t < NS; ++t)
           if (sl == t) {
-            wsel = w[t];
-            bsel = bv[t];
+            wsel = wf[t];
+            bsel = bf[t];
           }
-        const double wc = __shfl_sync(0xffffffffu, wsel, src);
-        const double bc = __shfl_sync(0xffffffffu, bsel, src);
+        const float2 wc = make_float2(__shfl_sync(0xffffffffu, wsel.x, src), __shfl_sync(0xffffffffu, wsel.y, src));
+        const float2 bc = make_float2(__shfl_sync(0xffffffffu, bsel.x, src), __shfl_sync(0xffffffffu, bsel.y, src));
 #pragma unroll
         for (int t = 0; t < NS; ++t) {
           const int cc = lane + 32 * t;
           if (cc < c) {
-            const double l = A[tri_off(K, cc) + c - cc];
-            w[t] = fma(-l, wc, w[t]);
-            bv[t] = fma(-l, bc, bv[t]);
+            const float2 l = d2f_trunc(A[tri_off(K, cc) + c - cc]);
+            df_fms(wf[t].x, wf[t].y, l, wc);
+            df_fms(bf[t].x, bf[t].y, l, bc);
           }
         }
+      }
+      double w[NS], bv[NS];
+#pragma unroll
+      for (int t = 0; t < NS; ++t) {
+        w[t] = f2d_scaled(wf[t].x, 0) + f2d_scaled(wf[t].y, 0);
+        bv[t] = f2d_scaled(bf[t].x, 0) + f2d_scaled(bf[t].y, 0);
       }
 #pragma unroll
       for (int t = 0; t < NS; ++t) {
