@@ -408,9 +408,96 @@ __device__ __forceinline__ void process_location(int64_t i, bool active, const F
     if (has1) A[w1 >> 16] = v1 ? val1 : 0.0;
   }
   __syncwarp();
-  // ---- L D L^T over the neighbour columns
+  // ---- L D L^T over the neighbour columns, two columns per step: column j, then column
+  // j+1 updated by column j and scaled, then one pass over the remaining prefix applying
+  // both (fma(-L1, T1, fma(-L0, T0, a)): the same roundings, in the same order, as two
+  // single-column steps, with half the column transitions and shared-memory passes).
   bool ok = true;
-  for (int j = 0; j < K - 1; ++j) {
+  double* __restrict__ TV1 = YV;  // column j+1's unscaled entries (YV is free after assembly)
+  int j = 0;
+  for (; j + 2 < K; j += 2) {
+    const int oj = tri_off(K, j), o1 = tri_off(K, j + 1);
+    const double d0 = A[oj];
+    ok = ok && pivot_in_range(d0);  // a failed block runs on (values unused) to stay in step
+    const double inv0 = rcp_fixed(d0);
+    for (int r = j + 1 + sub; r <= K; r += G) {
+      const double tv = A[oj + r - j];
+      TV[r] = tv;
+      if constexpr (G == 32) {
+        A[oj + r - j] = mul_by_positive(tv, inv0);
+      } else {
+        A[oj + r - j] = tv * inv0;
+      }
+    }
+    __syncwarp();
+    const double* L0 = A + oj - j;  // L0[r] = L[r][j]
+    {
+      const double t0 = TV[j + 1];
+      for (int r = j + 1 + sub; r <= K; r += G) {
+        const int e = o1 + r - j - 1;
+        A[e] = fma(-L0[r], t0, A[e]);
+      }
+    }
+    __syncwarp();
+    const double d1 = A[o1];
+    ok = ok && pivot_in_range(d1);
+    const double inv1 = rcp_fixed(d1);
+    for (int r = j + 2 + sub; r <= K; r += G) {
+      const double tv = A[o1 + r - j - 1];
+      TV1[r] = tv;
+      if constexpr (G == 32) {
+        A[o1 + r - j - 1] = mul_by_positive(tv, inv1);
+      } else {
+        A[o1 + r - j - 1] = tv * inv1;
+      }
+    }
+    __syncwarp();
+    const double* L1 = A + o1 - j - 1;  // L1[r] = L[r][j+1]
+    constexpr int U = 4;
+    const int nfull = (o1 - 1) / (G * U);
+    const int tail0 = 1 + G * U * nfull;
+    if (nfull > 0) {
+      double l0[U], t0[U], l1[U], t1[U], av[U];
+#pragma unroll
+      for (int k = 0; k < U; ++k) {
+        const uint32_t rc = sched[1 + sub + G * k];
+        l0[k] = L0[rc & 0xFF];
+        l1[k] = L1[rc & 0xFF];
+        t0[k] = TV[rc >> 8];
+        t1[k] = TV1[rc >> 8];
+        av[k] = A[1 + sub + G * k];
+      }
+      for (int bt = 0; bt < nfull; ++bt) {
+        const int base = 1 + sub + G * U * bt;
+        double res[U];
+#pragma unroll
+        for (int k = 0; k < U; ++k) res[k] = fma(-l0[k], t0[k], av[k]);
+#pragma unroll
+        for (int k = 0; k < U; ++k) res[k] = fma(-l1[k], t1[k], res[k]);
+        if (bt + 1 < nfull) {
+#pragma unroll
+          for (int k = 0; k < U; ++k) {
+            const int e = base + G * (U + k);
+            const uint32_t rc = sched[e];
+            l0[k] = L0[rc & 0xFF];
+            l1[k] = L1[rc & 0xFF];
+            t0[k] = TV[rc >> 8];
+            t1[k] = TV1[rc >> 8];
+            av[k] = A[e];
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < U; ++k) A[base + G * k] = res[k];
+      }
+    }
+    for (int e = tail0 + sub; e < o1; e += G) {
+      const uint32_t rc = sched[e];
+      const int r = rc & 0xFF, c = rc >> 8;
+      A[e] = fma(-L1[r], TV1[c], fma(-L0[r], TV[c], A[e]));
+    }
+    __syncwarp();
+  }
+  if (j < K - 1) {  // an odd number of neighbour columns: the last one alone
     const int oj = tri_off(K, j);
     const double d = A[oj];
     ok = ok && pivot_in_range(d);  // a failed block runs on (values unused) to stay in step
