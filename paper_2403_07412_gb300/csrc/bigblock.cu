@@ -152,44 +152,106 @@ __global__ void __launch_bounds__(kCtaThreadsMax) vecchia_big_kernel(const BigAr
       if (has1) A[tri_off(K, c1) + r1 - c1] = ok1 ? val1 : 0.0;
     }
     __syncthreads();
-    // ---- L D L^T over the neighbour columns (CTA-wide steps)
+    // ---- L D L^T over the neighbour columns (CTA-wide steps), two columns per step as in
+    // the warp kernels (bit-identical to single-column steps; YV is free after assembly)
     bool ok = true;
-    for (int j = 0; j < K - 1; ++j) {
-      const int oj = tri_off(K, j);
-      const double d = A[oj];
-      if (!pivot_in_range(d)) { ok = false; break; }  // uniform over the CTA
-      const double inv = rcp_fixed(d);
+    double* TV1 = YV;
+    int j = 0;
+    for (; j + 2 < K; j += 2) {
+      const int oj = tri_off(K, j), o1 = tri_off(K, j + 1);
+      const double d0 = A[oj];
+      if (!pivot_in_range(d0)) { ok = false; break; }  // uniform over the CTA
+      const double inv0 = rcp_fixed(d0);
       for (int r = j + 1 + tid; r <= K; r += NTH) {
         const double tv = A[oj + r - j];
         TV[r] = tv;
-        A[oj + r - j] = tv * inv;
+        A[oj + r - j] = tv * inv0;
       }
       __syncthreads();
-      const double* Lc = A + oj - j;
-      constexpr int U = 8;
-      const int nfull = (oj - 1) / (NTH * U);
+      const double* L0 = A + oj - j;
+      {
+        const double t0 = TV[j + 1];
+        for (int r = j + 1 + tid; r <= K; r += NTH) {
+          const int e = o1 + r - j - 1;
+          A[e] = fma(-L0[r], t0, A[e]);
+        }
+      }
+      __syncthreads();
+      const double d1 = A[o1];
+      if (!pivot_in_range(d1)) { ok = false; break; }
+      const double inv1 = rcp_fixed(d1);
+      for (int r = j + 2 + tid; r <= K; r += NTH) {
+        const double tv = A[o1 + r - j - 1];
+        TV1[r] = tv;
+        A[o1 + r - j - 1] = tv * inv1;
+      }
+      __syncthreads();
+      const double* L1 = A + o1 - j - 1;
+      constexpr int U = 4;
+      const int nfull = (o1 - 1) / (NTH * U);
       const int tail0 = 1 + NTH * U * nfull;
       for (int bt = 0; bt < nfull; ++bt) {
         const int base = 1 + tid + NTH * U * bt;
-        double lv[U], tv[U], av[U];
+        double l0[U], t0[U], l1[U], t1[U], av[U];
 #pragma unroll
         for (int k = 0; k < U; ++k) {
           const int e = base + NTH * k;
           const int w = tri_root(e);
           const int c = K - w, r = c + (e - w * (w + 1) / 2);
-          lv[k] = Lc[r];
-          tv[k] = TV[c];
+          l0[k] = L0[r];
+          l1[k] = L1[r];
+          t0[k] = TV[c];
+          t1[k] = TV1[c];
           av[k] = A[e];
         }
 #pragma unroll
-        for (int k = 0; k < U; ++k) A[base + NTH * k] = fma(-lv[k], tv[k], av[k]);
+        for (int k = 0; k < U; ++k) A[base + NTH * k] = fma(-l1[k], t1[k], fma(-l0[k], t0[k], av[k]));
       }
-      for (int e = tail0 + tid; e < oj; e += NTH) {
+      for (int e = tail0 + tid; e < o1; e += NTH) {
         const int w = tri_root(e);
         const int c = K - w, r = c + (e - w * (w + 1) / 2);
-        A[e] = fma(-Lc[r], TV[c], A[e]);
+        A[e] = fma(-L1[r], TV1[c], fma(-L0[r], TV[c], A[e]));
       }
       __syncthreads();
+    }
+    if (ok && j < K - 1) {  // an odd number of neighbour columns: the last one alone
+      do {
+        const int oj = tri_off(K, j);
+        const double d = A[oj];
+        if (!pivot_in_range(d)) { ok = false; break; }  // uniform over the CTA (leaves the do)
+        const double inv = rcp_fixed(d);
+        for (int r = j + 1 + tid; r <= K; r += NTH) {
+          const double tv = A[oj + r - j];
+          TV[r] = tv;
+          A[oj + r - j] = tv * inv;
+        }
+        __syncthreads();
+        const double* Lc = A + oj - j;
+        constexpr int U = 8;
+        const int nfull = (oj - 1) / (NTH * U);
+        const int tail0 = 1 + NTH * U * nfull;
+        for (int bt = 0; bt < nfull; ++bt) {
+          const int base = 1 + tid + NTH * U * bt;
+          double lv[U], tv[U], av[U];
+#pragma unroll
+          for (int k = 0; k < U; ++k) {
+            const int e = base + NTH * k;
+            const int w = tri_root(e);
+            const int c = K - w, r = c + (e - w * (w + 1) / 2);
+            lv[k] = Lc[r];
+            tv[k] = TV[c];
+            av[k] = A[e];
+          }
+#pragma unroll
+          for (int k = 0; k < U; ++k) A[base + NTH * k] = fma(-lv[k], tv[k], av[k]);
+        }
+        for (int e = tail0 + tid; e < oj; e += NTH) {
+          const int w = tri_root(e);
+          const int c = K - w, r = c + (e - w * (w + 1) / 2);
+          A[e] = fma(-Lc[r], TV[c], A[e]);
+        }
+        __syncthreads();
+      } while (false);
     }
     const double st = A[1], rr = A[2];
     const bool good = ok && positive_finite(st);
