@@ -58,6 +58,81 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return s;
 }
 
+// B columns j..j+B-1 of the bordered L D L^T, CTA-wide.  Each column in turn is scaled by
+// its pivot's reciprocal (its unscaled entries kept in TVs[q]) and applied to the later
+// columns of the group; then one pass over the remaining prefix [1, o_{j+B-1}) applies
+// all B columns to each slot in column order, fma(-L_q T_q, .) for q = 0..B-1.  Every
+// slot sees the same roundings in the same order as with single-column steps, while the
+// trailing matrix is read and written once per B columns.  Returns false (uniformly over
+// the CTA) at a pivot outside rcp_fixed's domain.
+template <int B>
+__device__ __forceinline__ bool cta_columns(double* A, double* const* TVs, int K, int j, int tid, int NTH) {
+  int o[B];
+#pragma unroll
+  for (int q = 0; q < B; ++q) o[q] = tri_off(K, j + q);
+#pragma unroll
+  for (int q = 0; q < B; ++q) {
+    const double d = A[o[q]];
+    if (!pivot_in_range(d)) return false;  // every thread reads the same pivot
+    const double inv = rcp_fixed(d);
+    double* T = TVs[q];
+    for (int r = j + q + 1 + tid; r <= K; r += NTH) {
+      const double tv = A[o[q] + r - j - q];
+      T[r] = tv;
+      A[o[q] + r - j - q] = tv * inv;
+    }
+    __syncthreads();
+    if (q + 1 < B) {
+      const double* Lq = A + o[q] - j - q;
+#pragma unroll
+      for (int p = q + 1; p < B; ++p) {
+        const double tp = T[j + p];
+        for (int r = j + p + tid; r <= K; r += NTH) {
+          const int e = o[p] + r - j - p;
+          A[e] = fma(-Lq[r], tp, A[e]);
+        }
+      }
+      __syncthreads();
+    }
+  }
+  const double* L[B];
+#pragma unroll
+  for (int q = 0; q < B; ++q) L[q] = A + o[q] - j - q;
+  constexpr int U = 8 / B;
+  const int end = o[B - 1];
+  const int nfull = (end - 1) / (NTH * U);
+  const int tail0 = 1 + NTH * U * nfull;
+  for (int bt = 0; bt < nfull; ++bt) {
+    const int base = 1 + tid + NTH * U * bt;
+    double av[U];
+    int rr[U], cc[U];
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      const int e = base + NTH * k;
+      const int w = tri_root(e);
+      cc[k] = K - w;
+      rr[k] = cc[k] + (e - w * (w + 1) / 2);
+      av[k] = A[e];
+    }
+#pragma unroll
+    for (int q = 0; q < B; ++q)
+#pragma unroll
+      for (int k = 0; k < U; ++k) av[k] = fma(-L[q][rr[k]], TVs[q][cc[k]], av[k]);
+#pragma unroll
+    for (int k = 0; k < U; ++k) A[base + NTH * k] = av[k];
+  }
+  for (int e = tail0 + tid; e < end; e += NTH) {
+    const int w = tri_root(e);
+    const int c = K - w, r = c + (e - w * (w + 1) / 2);
+    double a = A[e];
+#pragma unroll
+    for (int q = 0; q < B; ++q) a = fma(-L[q][r], TVs[q][c], a);
+    A[e] = a;
+  }
+  __syncthreads();
+  return true;
+}
+
 template <bool GRAD, bool SPHERE>
 __global__ void __launch_bounds__(kCtaThreadsMax) vecchia_big_kernel(const BigArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -152,107 +227,14 @@ __global__ void __launch_bounds__(kCtaThreadsMax) vecchia_big_kernel(const BigAr
       if (has1) A[tri_off(K, c1) + r1 - c1] = ok1 ? val1 : 0.0;
     }
     __syncthreads();
-    // ---- L D L^T over the neighbour columns (CTA-wide steps), two columns per step as in
-    // the warp kernels (bit-identical to single-column steps; YV is free after assembly)
+    // ---- L D L^T over the neighbour columns: CTA-wide steps of four columns (then two,
+    // then one), bit-identical to single-column steps (cta_columns)
+    double* TVs[4] = {TV, YV, WH, GV};  // YV, WH and GV are free during the elimination
     bool ok = true;
-    double* TV1 = YV;
     int j = 0;
-    for (; j + 2 < K; j += 2) {
-      const int oj = tri_off(K, j), o1 = tri_off(K, j + 1);
-      const double d0 = A[oj];
-      if (!pivot_in_range(d0)) { ok = false; break; }  // uniform over the CTA
-      const double inv0 = rcp_fixed(d0);
-      for (int r = j + 1 + tid; r <= K; r += NTH) {
-        const double tv = A[oj + r - j];
-        TV[r] = tv;
-        A[oj + r - j] = tv * inv0;
-      }
-      __syncthreads();
-      const double* L0 = A + oj - j;
-      {
-        const double t0 = TV[j + 1];
-        for (int r = j + 1 + tid; r <= K; r += NTH) {
-          const int e = o1 + r - j - 1;
-          A[e] = fma(-L0[r], t0, A[e]);
-        }
-      }
-      __syncthreads();
-      const double d1 = A[o1];
-      if (!pivot_in_range(d1)) { ok = false; break; }
-      const double inv1 = rcp_fixed(d1);
-      for (int r = j + 2 + tid; r <= K; r += NTH) {
-        const double tv = A[o1 + r - j - 1];
-        TV1[r] = tv;
-        A[o1 + r - j - 1] = tv * inv1;
-      }
-      __syncthreads();
-      const double* L1 = A + o1 - j - 1;
-      constexpr int U = 4;
-      const int nfull = (o1 - 1) / (NTH * U);
-      const int tail0 = 1 + NTH * U * nfull;
-      for (int bt = 0; bt < nfull; ++bt) {
-        const int base = 1 + tid + NTH * U * bt;
-        double l0[U], t0[U], l1[U], t1[U], av[U];
-#pragma unroll
-        for (int k = 0; k < U; ++k) {
-          const int e = base + NTH * k;
-          const int w = tri_root(e);
-          const int c = K - w, r = c + (e - w * (w + 1) / 2);
-          l0[k] = L0[r];
-          l1[k] = L1[r];
-          t0[k] = TV[c];
-          t1[k] = TV1[c];
-          av[k] = A[e];
-        }
-#pragma unroll
-        for (int k = 0; k < U; ++k) A[base + NTH * k] = fma(-l1[k], t1[k], fma(-l0[k], t0[k], av[k]));
-      }
-      for (int e = tail0 + tid; e < o1; e += NTH) {
-        const int w = tri_root(e);
-        const int c = K - w, r = c + (e - w * (w + 1) / 2);
-        A[e] = fma(-L1[r], TV1[c], fma(-L0[r], TV[c], A[e]));
-      }
-      __syncthreads();
-    }
-    if (ok && j < K - 1) {  // an odd number of neighbour columns: the last one alone
-      do {
-        const int oj = tri_off(K, j);
-        const double d = A[oj];
-        if (!pivot_in_range(d)) { ok = false; break; }  // uniform over the CTA (leaves the do)
-        const double inv = rcp_fixed(d);
-        for (int r = j + 1 + tid; r <= K; r += NTH) {
-          const double tv = A[oj + r - j];
-          TV[r] = tv;
-          A[oj + r - j] = tv * inv;
-        }
-        __syncthreads();
-        const double* Lc = A + oj - j;
-        constexpr int U = 8;
-        const int nfull = (oj - 1) / (NTH * U);
-        const int tail0 = 1 + NTH * U * nfull;
-        for (int bt = 0; bt < nfull; ++bt) {
-          const int base = 1 + tid + NTH * U * bt;
-          double lv[U], tv[U], av[U];
-#pragma unroll
-          for (int k = 0; k < U; ++k) {
-            const int e = base + NTH * k;
-            const int w = tri_root(e);
-            const int c = K - w, r = c + (e - w * (w + 1) / 2);
-            lv[k] = Lc[r];
-            tv[k] = TV[c];
-            av[k] = A[e];
-          }
-#pragma unroll
-          for (int k = 0; k < U; ++k) A[base + NTH * k] = fma(-lv[k], tv[k], av[k]);
-        }
-        for (int e = tail0 + tid; e < oj; e += NTH) {
-          const int w = tri_root(e);
-          const int c = K - w, r = c + (e - w * (w + 1) / 2);
-          A[e] = fma(-Lc[r], TV[c], A[e]);
-        }
-        __syncthreads();
-      } while (false);
-    }
+    for (; ok && j + 4 < K; j += 4) ok = cta_columns<4>(A, TVs, K, j, tid, NTH);
+    for (; ok && j + 2 < K; j += 2) ok = cta_columns<2>(A, TVs, K, j, tid, NTH);
+    if (ok && j + 1 < K) ok = cta_columns<1>(A, TVs, K, j, tid, NTH);
     const double st = A[1], rr = A[2];
     const bool good = ok && positive_finite(st);
     const double nan = __longlong_as_double(0x7FF8000000000000LL);
