@@ -404,9 +404,11 @@ def test_powexp_likelihood_terms_match_oracle(V, alpha):
         assert abs(tot[k] - ref[k]) <= W.GRAD_RTOL * np.abs(want[:, k]).sum(), (k, tot[k], ref[k])
 
 
-@pytest.mark.parametrize("m", [64, 90, 150])
+@pytest.mark.parametrize("m", [64, 67, 90, 150])
 def test_large_conditioning_sets_match_oracle(V, m):
-    # m beyond the warp kernels: one CTA per location (the paper runs m up to 150).
+    # m beyond the warp kernels: one CTA per location (the paper runs m up to 150).  The
+    # m neighbour columns are eliminated four at a time, then two, then one: m = 64, 90
+    # and 150 leave no column, two and two; m = 67 leaves three (a pair and a single).
     n = 1200
     theta = (1.3, 0.08, 1.0, 0.02)
     xy = datagen.uniform_locations(n, 100 + m)
