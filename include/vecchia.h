@@ -152,14 +152,18 @@ int vecchia_plan_neighbors(vecchia_plan_t plan, int32_t* nbr_out);
  *   out_dev : 1 double on the device: l.
  * Asynchronous on `stream`.  Errors returned: EINVAL (bad theta, NULL pointers),
  * ECUDA.  A non-positive-definite block makes out_dev NaN (see
- * vecchia_last_error_location).
+ * vecchia_last_error_location); a block counts as such when a pivot of its elimination
+ * falls outside [2^-1022, 2^1022) (see vecchia_pivot_reciprocal) or its conditional
+ * variance is not positive and finite.
  */
 int vecchia_loglik(vecchia_plan_t plan, const double* y_dev, const double theta[4], double* out_dev,
                    void* stream);
 
 /*
  * vecchia_loglik_grad — l and its gradient (not in the paper: the adjoint of Algorithm 1
- * with respect to sigma2, beta and tau2, recomputing each block's factor).
+ * with respect to sigma2, beta and tau2, recomputing each block's factor).  l is computed
+ * exactly as by vecchia_loglik (FP64 elimination); the adjoint's two backward solves and
+ * its beta pair sums run in double-float arithmetic (about 2^-46 relative per operation).
  *   out_dev : 4 doubles on the device: {l, dl/dsigma2, dl/dbeta, dl/dtau2}.
  * Same arguments, asynchrony and errors as vecchia_loglik.
  */
