@@ -46,6 +46,12 @@ def la_flops(n: int, m: int, grad: bool) -> float:
     return float(f.sum())
 
 
+def workload_label(n: int, m: int, order: str, fwd: bool) -> str:
+    """The config's workload name; the default arguments give WORKLOAD."""
+    n_label = "1M" if n == 1_000_000 else str(n)
+    return f"vecchia-matern-gmm{n_label}-{order}-m{m}-nu1.0-{'fwd' if fwd else 'fwd+grad'}"
+
+
 def kernel_source_hash() -> str:
     """Hash of the CUDA sources with comments and blank space removed, so that the DRAM
     counters in profiles/traffic.json stay attached to the code they were taken on."""
@@ -342,7 +348,7 @@ def run_reference(args, rank, world):
     import oracle
 
     oracle.build()
-    n, m = args.n, 60
+    n, m = args.n, args.m
     xy, y, theta = make_workload(n, None, 0)
     perm = oracle.order_random(n, 99)
     xo, yo = xy[perm], y[perm]
@@ -368,7 +374,8 @@ def run_reference(args, rank, world):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "locations/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": n, "m": m, "ordering": "random (oracle's own)",
+        "config": {"workload": workload_label(n, m, args.order, False), "n": n, "m": m,
+                   "ordering": "random (oracle's own)",
                    "theta": list(theta), "sample_locations_per_step": rows_n},
         "cpu_baseline": {"value": value, "unit": "locations/s", "cores": oracle.num_threads(), "kind": "oracle",
                          "sample": f"{rows_n} random locations of the {n}-location workload per step"},
@@ -525,13 +532,18 @@ def main():
         try:
             tj = json.load(open(traffic_path))
             key = "fwd" if args.fwd else "grad"
-            if tj.get("n") == n and tj.get("m") == m and tj.get("source_hash") == kernel_source_hash():
+            if (tj.get("n") == n and tj.get("m") == m and tj.get("order", "maxmin") == args.order
+                    and tj.get("source_hash") == kernel_source_hash()):
                 traffic = tj.get(key)
         except Exception:
             traffic = None
     hbm_gbs = traffic / (kern_ms * 1e-3) / 1e9 if traffic else None
     cov_evals = float(sum(min(i, m) * (min(i, m) + 1) // 2 for i in range(min(n, m + 1)))) + \
         float(max(n - (m + 1), 0)) * (m * (m + 1) // 2)
+    # labels follow the arguments; the defaults give WORKLOAD and the warp kernel
+    workload = workload_label(n, m, args.order, args.fwd)
+    kern_name = ("vecchia_big_kernel" if m > 63 else "vecchia_lik_kernel") + ("<false>" if args.fwd else "<true>")
+    step_bytes = n * (16 + 8 + 4 * m)
     line = {
         "metric": METRIC,
         "value": value,
@@ -546,18 +558,20 @@ def main():
         "dtype": "f64",
         "data": "synthetic",
         "config": {
-            "workload": WORKLOAD if not args.fwd else WORKLOAD.replace("fwd+grad", "fwd"),
+            "workload": workload,
             "n": n, "m": m, "ordering": args.order, "theta": list(theta),
             "locations": "20-component Gaussian mixture in [0,1]^2",
             "field": "random Fourier features, 4096, Matern nu=1.0",
-            "l2": "inputs exceed L2 (264 MB per step: 240 MB neighbour table, 16 MB coordinates, 8 MB field)",
+            "l2": (f"inputs {'exceed' if step_bytes > 129e6 else 'fit in'} L2 ({step_bytes / 1e6:.0f} MB per step: "
+                   f"{n * 4 * m / 1e6:.0f} MB neighbour table, {n * 16 / 1e6:.0f} MB coordinates, "
+                   f"{n * 8 / 1e6:.0f} MB field)"),
             "plan_seconds": round(plan_s, 3),
             "result_finite": ok,
             "parallelism": f"{world} independent fields (one per GPU)",
         },
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": "vecchia_lik_kernel<true>" if not args.fwd else "vecchia_lik_kernel<false>",
+                     "kernel": kern_name,
                      "flops_per_launch": flops,
                      "peak_source": "FP64 DFMA-chain kernel measured in this run (vecchia_fp64_peak)"},
         "covariance": {"entries_per_call": cov_evals, "entries_per_s": cov_evals / (kern_ms * 1e-3),
