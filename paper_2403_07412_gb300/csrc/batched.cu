@@ -282,6 +282,20 @@ int build_batch(const Plan* const* plans, const double* const* ys, int nfields, 
     d.item_base = items;
     items += (int64_t)d.tiles * ntheta;
   }
+  // Every warp's shared-memory area is sized for the largest field's share (32/lanes
+  // blocks).  A field whose own choice of lanes would need more than the full-warp
+  // fields do widens its groups instead, so the launch keeps the occupancy of the
+  // largest blocks (which carry most of the flops).
+  int full_area = 0;
+  for (int f = 0; f < nfields; ++f)
+    if (fd[f].lanes == 32) full_area = std::max(full_area, WarpArea::doubles(fd[f].m + 1, want_grad != 0));
+  if (full_area > 0) {
+    for (int f = 0; f < nfields; ++f) {
+      const int K = fd[f].m + 1;
+      while (fd[f].lanes < 32 && (32 / fd[f].lanes) * WarpArea::doubles(K, want_grad != 0) > full_area)
+        fd[f].lanes *= 2;
+    }
+  }
   for (int s = 0; s < nfields; ++s) {
     b->plans.push_back(plans[s]);
     b->ys.push_back(ys[s]);
