@@ -53,14 +53,18 @@ def workload_label(n: int, m: int, order: str, fwd: bool) -> str:
 
 
 def kernel_source_hash() -> str:
-    """Hash of the CUDA sources with comments and blank space removed, so that the DRAM
-    counters in profiles/traffic.json stay attached to the code they were taken on."""
+    """Hash of the likelihood kernel's sources (its translation unit loglik.cu, every
+    header, and matern.cu, which builds the table the kernel reads) with comments and blank
+    space removed, so that the DRAM counters in profiles/traffic.json stay attached to the
+    code they were taken on."""
     import glob
     import hashlib
     import re
 
+    csrc = os.path.join(ROOT, "paper_2403_07412_gb300", "csrc")
+    files = [os.path.join(csrc, "loglik.cu"), os.path.join(csrc, "matern.cu")] + glob.glob(os.path.join(csrc, "*.cuh"))
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2403_07412_gb300", "csrc", "*.cu*"))):
+    for f in sorted(files):
         src = open(f, encoding="utf-8").read()
         src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
         src = re.sub(r"//[^\n]*", "", src)
