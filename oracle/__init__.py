@@ -10,7 +10,8 @@ What each function follows:
 * :func:`matern` — Eq. (2) (Sec. IV-A), through ``std::cyl_bessel_k``;
   :func:`powexp` — Eq. (3), the power-exponential family of the real-data model.
 * :func:`loglik_exact` — Eq. (1), dense, with the oracle's own Cholesky.
-* :func:`order_random` / :func:`order_maxmin` / :func:`order_morton` — Sec. V-A
+* :func:`order_random` / :func:`order_maxmin` (and its prefix,
+  :func:`order_maxmin_prefix`) / :func:`order_morton` — Sec. V-A
   orderings (random = splitmix64-driven Fisher–Yates; maxmin = greedy farthest
   point from the point nearest the centroid, ties to the lowest index; Morton =
   Z-order of 16-bit cell indices).
@@ -80,6 +81,7 @@ def _load():
             "oracle_splitmix64": (None, [c_u64, c_i64, _u64p]),
             "oracle_order_random": (c_int, [c_i64, c_u64, _i64p]),
             "oracle_order_maxmin": (c_int, [c_i64, _dp, _i64p]),
+            "oracle_order_maxmin_prefix": (c_int, [c_i64, _dp, c_i64, _i64p]),
             "oracle_order_morton": (c_int, [c_i64, _dp, _i64p]),
             "oracle_knn_rows": (c_int, [c_i64, _dp, c_i32, _i64p, c_i64, _i32p]),
             "oracle_vecchia_rows": (c_int, [c_i64, _dp, _dp, c_i32, _dp, _i64p, c_i64, _i32p, c_int,
@@ -175,6 +177,16 @@ def order_maxmin(xy) -> np.ndarray:
     xy = _f64(xy).reshape(-1, 2)
     perm = np.empty(xy.shape[0], dtype=np.int64)
     _load().oracle_order_maxmin(xy.shape[0], _p(xy, _dp), _p(perm, _i64p))
+    return perm
+
+
+def order_maxmin_prefix(xy, count: int) -> np.ndarray:
+    """The first ``count`` entries of :func:`order_maxmin` (same greedy steps, stopped early;
+    O(count * n))."""
+    xy = _f64(xy).reshape(-1, 2)
+    perm = np.empty(int(count), dtype=np.int64)
+    if _load().oracle_order_maxmin_prefix(xy.shape[0], _p(xy, _dp), int(count), _p(perm, _i64p)):
+        raise ValueError("order_maxmin_prefix: count exceeds n")
     return perm
 
 

@@ -396,8 +396,11 @@ int oracle_order_random(int64_t n, uint64_t seed, int64_t* perm) {
 // nearest the centroid (sums in index order), then repeatedly take the point
 // whose minimum squared distance to the chosen set is largest; ties go to the
 // lowest original index.  O(n^2), parallel over points.
-int oracle_order_maxmin(int64_t n, const double* xy, int64_t* perm) {
-  if (n <= 0) return 0;
+// oracle_order_maxmin_prefix stops after the first `count` picks (perm holds count
+// entries): the same greedy steps, so its output is a prefix of the full ordering.
+int oracle_order_maxmin_prefix(int64_t n, const double* xy, int64_t count, int64_t* perm) {
+  if (n <= 0 || count <= 0) return 0;
+  if (count > n) return 1;
   double sx = 0.0, sy = 0.0;
   for (int64_t i = 0; i < n; ++i) { sx += xy[2 * i]; sy += xy[2 * i + 1]; }
   const double c[2] = {sx / (double)n, sy / (double)n};
@@ -412,7 +415,7 @@ int oracle_order_maxmin(int64_t n, const double* xy, int64_t* perm) {
   perm[0] = first;
   used[first] = 1;
   int64_t last = first;
-  for (int64_t k = 1; k < n; ++k) {
+  for (int64_t k = 1; k < count; ++k) {
     double gbest = -1.0;
     int64_t gidx = -1;
 #pragma omp parallel
@@ -436,6 +439,10 @@ int oracle_order_maxmin(int64_t n, const double* xy, int64_t* perm) {
     last = gidx;
   }
   return 0;
+}
+
+int oracle_order_maxmin(int64_t n, const double* xy, int64_t* perm) {
+  return oracle_order_maxmin_prefix(n, xy, n, perm);
 }
 
 // Morton ordering (Sec. V-A and Fig. 1, the Z-order alternative to random ordering):

@@ -156,6 +156,18 @@ def test_order_maxmin_matches_brute_force(oracle_mod):
         np.testing.assert_array_equal(oracle_mod.order_maxmin(xy), _maxmin_brute(xy))
 
 
+def test_order_maxmin_prefix_is_the_leading_part(oracle_mod):
+    # The stopped-early form takes the same greedy steps: its output is the first
+    # `count` entries of numpy brute force (and of the full ordering).
+    xy = datagen.gmm_locations(500, 9)
+    full = _maxmin_brute(xy)
+    for count in (1, 2, 37, 500):
+        np.testing.assert_array_equal(oracle_mod.order_maxmin_prefix(xy, count), full[:count])
+    np.testing.assert_array_equal(oracle_mod.order_maxmin(xy), full)
+    with pytest.raises(ValueError):
+        oracle_mod.order_maxmin_prefix(xy, 501)
+
+
 def test_order_maxmin_grid_structure(oracle_mod):
     # 3x3 grid: start at the centre; then the four corners (each at squared distance
     # 0.5 from the centre, ties to the lowest index), then the edge midpoints.
