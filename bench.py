@@ -12,8 +12,19 @@ and the result copied back every step.  ``roofline`` rates the dominant kernel
 (vecchia_lik_kernel, fwd+adjoint) against the FP64 FMA peak measured in the same run.
 ``cpu_baseline`` times the CPU oracle on a bounded sample of the same workload.
 
-Multi-GPU (torchrun, N > 1): every rank evaluates its own independent field of the same
-shape (weak scaling; no collective on the data path); value = N * n / max step time.
+``roofline.achieved`` counts the algorithmic linear-algebra flops of the likelihood,
+F(k) = k^3/3 + k^2/2 + k/6 + k^2 per location (k = m_i + 1), for the forward and the
+forward + gradient step alike; ``roofline.frac_with_adjoint_solves`` adds the adjoint's
+two unit triangular solves (2 m_i^2 per location).  ``configs`` times the other
+workloads (2k / 100k forward, 250k forward + gradient) as lines of their own.
+
+Multi-GPU (torchrun, N > 1), ``--shard locations`` (default): one field of n locations,
+its ordered locations split into N contiguous ranges (shard.location_ranges); every rank
+holds the same plan, evaluates its range with vecchia_loglik_range and the ranks sum the
+four result doubles with one NCCL all-reduce per step; value = n / max step time (strong
+scaling: the job's work is fixed).  ``--shard fields``: every rank evaluates its own
+independent field of n locations (weak scaling; no collective on the data path); value =
+N * n / max step time.
 """
 import argparse
 import json
@@ -37,7 +48,12 @@ def la_flops(n: int, m: int, grad: bool) -> float:
     """Algorithmic FP64 flops of one evaluation: per location k = m_i + 1,
     k^3/3 + k^2/2 + k/6 (Cholesky) + k^2 (two triangular solves); the adjoint adds
     two unit triangular solves of size m_i (2 m_i^2)."""
-    i = np.arange(n, dtype=np.float64)
+    return la_flops_range(0, n, m, grad)
+
+
+def la_flops_range(i0: int, i1: int, m: int, grad: bool) -> float:
+    """la_flops over the ordered locations [i0, i1)."""
+    i = np.arange(i0, i1, dtype=np.float64)
     mi = np.minimum(i, m)
     k = mi + 1
     f = k ** 3 / 3 + k ** 2 / 2 + k / 6 + k ** 2
@@ -128,6 +144,26 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        fields = dict(ln.split(":", 1) for ln in out.splitlines() if ":" in ln)
+        name = fields.get("Model name", "").strip()
+        vendor = fields.get("Vendor ID", "").strip()
+        if name:
+            return f"{vendor} {name}".strip()
+    except Exception:
+        pass
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith(("model name", "cpu model", "hardware")):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
 def make_workload(n, device, rank):
     from paper_2403_07412_gb300 import datagen
 
@@ -197,6 +233,101 @@ def run_batched(V, dev, peak_tflops, nfields=64, ntheta=32, scale=1.0, reps=1):
             "location_evaluations": int(locs), "graph_replays_timed": reps,
             "frac_of_fp64_peak": achieved / peak_tflops, "achieved_tflops": achieved,
             "result_finite": bool(np.all(np.isfinite(res))), "setup_seconds": round(setup_s, 1)}
+
+
+def _time_call(fn, reps):
+    import torch
+
+    fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def run_configs(V, dev, peak_tflops):
+    """The other workloads of the study as lines of their own (seeds as in the tests):
+    2,000 uniform locations with an exactly drawn field (nu = 0.5, m = 10, forward);
+    100,000 uniform, random-Fourier-feature field (nu = 1.5, tau2 = 0.01, m = 30,
+    forward); 250,000 uniform (nu = 2.5, tau2 = 0.05, m = 60, forward + gradient).  All
+    random ordering.  frac counts F(k) per location as the headline's roofline does."""
+    import torch
+    from paper_2403_07412_gb300 import datagen
+
+    B = datagen.BASE_SEED
+    specs = [
+        ("uniform2k-exact-nu0.5-m10-fwd", 2_000, (1.0, 0.1, 0.5, 0.0), 10, B + 1, False, True, 200),
+        ("uniform100k-rff-nu1.5-m30-fwd", 100_000, (1.0, 0.05, 1.5, 0.01), 30, B + 2, False, False, 20),
+        ("uniform250k-rff-nu2.5-m60-fwd+grad", 250_000, (1.5, 0.03, 2.5, 0.05), 60, B + 3, True, False, 10),
+    ]
+    rows = []
+    for name, n, theta, m, seed, grad, exact, reps in specs:
+        xy = datagen.uniform_locations(n, seed)
+        y = datagen.field_dense(xy, theta, seed + 1000) if exact else datagen.field_rff(xy, theta, seed + 1000,
+                                                                                        device=dev)
+        yd = torch.as_tensor(y, device=dev)
+        plan = V.Plan(xy, m, order=V.ORDER_RANDOM, seed=seed)
+        out = torch.empty(4, dtype=torch.float64, device=dev)
+        fn = V.vecchia_loglik_grad if grad else V.vecchia_loglik
+        ms_call = _time_call(lambda: fn(plan, yd, theta, out=out), reps)
+        tf = la_flops(n, m, False) / (ms_call * 1e-3) / 1e12
+        rows.append({"workload": f"vecchia-matern-{name}", "n": n, "m": m, "theta": list(theta),
+                     "ms_per_call": round(ms_call, 4), "value": n / (ms_call * 1e-3), "unit": "locations/s",
+                     "frac_of_fp64_peak": round(tf / peak_tflops, 4), "result_finite": bool(
+                         np.all(np.isfinite(out[: 4 if grad else 1].cpu().numpy())))})
+        plan.close()
+    return rows
+
+
+def run_nu_steps(V, dev, n=100_000, m=30, steps=8):
+    """Smoothness estimation: wall time per step of the differentiable likelihood
+    (VecchiaLogLik forward + backward: the adjoint call plus two forward calls at nu +/- h
+    for the nu derivative), each step at a smoothness not seen before (so two covariance
+    tables are built per step), against the same steps at one cached nu; and an L-BFGS-B
+    fit of (sigma2, beta, nu, tau2) on a 20k-location field, per likelihood evaluation."""
+    import torch
+    from paper_2403_07412_gb300 import datagen, mle
+
+    seed = datagen.BASE_SEED + 2
+    theta0 = (1.0, 0.05, 1.5, 0.01)
+    xy = datagen.uniform_locations(n, seed)
+    yd = torch.as_tensor(datagen.field_rff(xy, theta0, seed + 1000, device=dev), device=dev)
+    plan = V.Plan(xy, m, order=V.ORDER_RANDOM, seed=seed)
+
+    def step(nu):
+        th = torch.tensor([theta0[0], theta0[1], nu, theta0[3]], dtype=torch.float64, requires_grad=True)
+        V.VecchiaLogLik.apply(th, plan, yd).backward()
+        torch.cuda.synchronize()
+
+    step(1.5)
+    t0 = time.perf_counter()
+    for k in range(steps):
+        step(1.5 + 0.0123 * (k + 1))
+    fresh = (time.perf_counter() - t0) / steps
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        step(1.5)
+    cached = (time.perf_counter() - t0) / steps
+    plan.close()
+    n2 = 20_000
+    xy2 = datagen.uniform_locations(n2, seed + 7)
+    y2 = torch.as_tensor(datagen.field_rff(xy2, theta0, seed + 1007, device=dev), device=dev)
+    p2 = V.Plan(xy2, m, order=V.ORDER_RANDOM, seed=seed)
+    t0 = time.perf_counter()
+    res = mle.fit(p2, y2, (0.8, 0.08, 1.0, 0.02), estimate_nu=True, max_iter=40)
+    fit_s = time.perf_counter() - t0
+    p2.close()
+    return {"workload": f"{n} uniform locations, m = {m}, Matern, autograd step at a new nu each step",
+            "ms_per_step_new_nu": round(fresh * 1e3, 3), "ms_per_step_cached_nu": round(cached * 1e3, 3),
+            "table_builds_per_step": 2,
+            "mle_fit": {"n": n2, "m": m, "evaluations": res.evaluations, "seconds": round(fit_s, 3),
+                        "ms_per_evaluation": round(fit_s / max(res.evaluations, 1) * 1e3, 3),
+                        "theta_hat": [round(float(v), 5) for v in res.theta], "converged": res.converged}}
 
 
 def run_m_sweep(V, dev, peak_tflops, n=250_000, ms=(10, 30, 60, 90, 120, 150)):
@@ -301,26 +432,31 @@ def run_predict(V, dev, n=250_000, n_new=25_000, m=30):
             "mean_predictive_var": float(var.mean().item())}
 
 
-def cpu_baseline(xy, y, theta, m, budget_s):
-    """The oracle, as it stands, on a bounded random sample of rows of the same workload
-    (its own random ordering and brute-force conditioning sets; neighbour search untimed)."""
+def cpu_baseline(xy, y, theta, m, budget_s, perm, nbr):
+    """The oracle, as it stands, on a bounded random sample of the timed plan's own rows:
+    the GPU plan's maxmin ordering ``perm`` and conditioning sets ``nbr`` (ordered
+    indices) are handed to the oracle's per-location evaluation, so both sides compute
+    the same terms.  The plan (ordering, neighbour search) is excluded from the timing;
+    the oracle's own brute-force neighbour search and maxmin ordering are timed apart."""
     import oracle
 
     oracle.build()
     n = xy.shape[0]
-    perm = oracle.order_random(n, 99)
     xo, yo = xy[perm], y[perm]
     rng = np.random.default_rng(0)
     probe = np.sort(rng.choice(np.arange(m + 1, n), 64, replace=False))
-    nb = oracle.knn_rows(xo, m, probe)
+    nb = np.ascontiguousarray(nbr[probe])
     t0 = time.perf_counter()
     oracle.vecchia_rows(xo, yo, m, theta, rows=probe, nbr=nb, want_grad=True)
     per_row = (time.perf_counter() - t0) / probe.size
     rows_n = int(max(64, min(200_000, budget_s / max(per_row, 1e-7))))
     rows = np.sort(rng.choice(np.arange(m + 1, n), rows_n, replace=False))
+    nb = np.ascontiguousarray(nbr[rows])
+    knn_rows = rows[: max(64, rows_n // 8)]
     t0 = time.perf_counter()
-    nb = oracle.knn_rows(xo, m, rows)
+    nb_oracle = oracle.knn_rows(xo, m, knn_rows)
     knn_s = time.perf_counter() - t0
+    knn_same = bool(np.array_equal(nb_oracle, nb[: knn_rows.size]))
     t0 = time.perf_counter()
     oracle.vecchia_rows(xo, yo, m, theta, rows=rows, nbr=nb, want_grad=True)
     dt = time.perf_counter() - t0
@@ -338,10 +474,14 @@ def cpu_baseline(xy, y, theta, m, budget_s):
     oracle.order_maxmin(sub)
     mm_s = time.perf_counter() - t0
     return {"value": rows_n / dt, "unit": "locations/s", "cores": cores, "kind": "oracle",
-            "sample": f"{rows_n} random locations (i > m) of the same 1M-location workload, loglik+grad, "
-                      f"oracle's own random ordering and brute-force neighbour sets (timed apart); {dt:.1f} s wall",
+            "cpu_model": cpu_model(), "nproc": os.cpu_count(),
+            "sample": f"{rows_n} random locations (i > m) of the timed {n}-location plan, loglik+grad, "
+                      f"the plan's own maxmin ordering and conditioning sets; {dt:.1f} s wall",
+            "same_config": True,
+            "excludes": "the plan (ordering and neighbour search), on both sides",
             "single_thread": {"value": one.size / dt1, "unit": "locations/s", "sample": f"{one.size} of the same rows"},
-            "knn_rows_per_s": rows_n / knn_s,
+            "knn_rows_per_s": knn_rows.size / knn_s,
+            "knn_rows_match_plan": knn_same,
             "maxmin_100k_s": round(mm_s, 3)}
 
 
@@ -382,7 +522,10 @@ def run_reference(args, rank, world):
                    "ordering": "random (oracle's own)",
                    "theta": list(theta), "sample_locations_per_step": rows_n},
         "cpu_baseline": {"value": value, "unit": "locations/s", "cores": oracle.num_threads(), "kind": "oracle",
-                         "sample": f"{rows_n} random locations of the {n}-location workload per step"},
+                         "cpu_model": cpu_model(), "nproc": os.cpu_count(),
+                         "sample": f"{rows_n} random locations of the {n}-location workload per step "
+                                   "(the oracle's own random ordering and brute-force conditioning sets)",
+                         "excludes": "the ordering and neighbour search (done once, untimed)"},
         "e2e": {"value": value, "unit": "locations/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -406,6 +549,9 @@ def main():
     ap.add_argument("--no-sphere", action="store_true", help="skip the great-circle workload")
     ap.add_argument("--no-predict", action="store_true", help="skip the kriging workload")
     ap.add_argument("--batched-scale", type=float, default=1.0, help="scale of the batched fields' sizes")
+    ap.add_argument("--no-configs", action="store_true", help="skip the other workloads' lines")
+    ap.add_argument("--shard", default="locations", choices=["locations", "fields"],
+                    help="N > 1: split one field's locations across ranks, or one independent field per rank")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -437,9 +583,13 @@ def main():
         dist.barrier()
     from paper_2403_07412_gb300 import vecchia as V
 
+    from paper_2403_07412_gb300 import shard
+
     dev = torch.device("cuda", local)
     n, m = args.n, args.m
-    xy, y, theta = make_workload(n, dev, rank)
+    split = world > 1 and args.shard == "locations"
+    # one field shared by all ranks (location split), or one field per rank
+    xy, y, theta = make_workload(n, dev, 0 if args.shard == "locations" else rank)
     t0 = time.perf_counter()
     plan = V.Plan(xy, m, order=V.ORDER_MAXMIN if args.order == "maxmin" else V.ORDER_RANDOM, seed=5)
     torch.cuda.synchronize()
@@ -447,7 +597,14 @@ def main():
     yd = torch.as_tensor(y, device=dev)
     out = torch.empty(4, dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream(dev)
-    call = V.vecchia_loglik if args.fwd else V.vecchia_loglik_grad
+    fn = V.vecchia_loglik if args.fwd else V.vecchia_loglik_grad
+    r0, r1 = shard.location_ranges(n, world)[rank] if split else (0, n)
+
+    def call(plan, yd, theta, out):
+        if split:  # this rank's range, then one all-reduce of the result doubles
+            return shard.loglik_sharded(plan, yd, theta, rank, world, want_grad=not args.fwd, out=out)
+        return fn(plan, yd, theta, out=out)
+
     peak_gflops = V.vecchia_fp64_peak()
 
     for _ in range(args.warmup):
@@ -478,7 +635,8 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
     ms_per_step = total_ms / args.steps
-    value = world * n / (ms_per_step * 1e-3)
+    job_locations = n if (split or world == 1) else world * n
+    value = job_locations / (ms_per_step * 1e-3)
     res = out.cpu().numpy()
     ok = bool(np.all(np.isfinite(res)))
 
@@ -524,7 +682,9 @@ def main():
         if dist is not None:
             dist.destroy_process_group()
         return
-    flops = la_flops(n, m, grad=not args.fwd)
+    # rank 0's kernel processes its own range [r0, r1) (all n on one GPU)
+    flops = la_flops_range(r0, r1, m, grad=False)
+    flops_adj = la_flops_range(r0, r1, m, grad=not args.fwd)
     kern_ms = statistics.mean(step_ms)
     achieved = flops / (kern_ms * 1e-3) / 1e12
     peak = peak_gflops / 1e3
@@ -557,7 +717,7 @@ def main():
         "warmup": args.warmup,
         "ms_per_step": ms_per_step,
         "higher_is_better": True,
-        "scaling": "weak",
+        "scaling": "strong" if args.shard == "locations" else "weak",
         "vs_baseline": None,
         "dtype": "f64",
         "data": "synthetic",
@@ -571,17 +731,22 @@ def main():
                    f"{n * 8 / 1e6:.0f} MB field)"),
             "plan_seconds": round(plan_s, 3),
             "result_finite": ok,
-            "parallelism": f"{world} independent fields (one per GPU)",
+            "parallelism": (f"one field, ordered locations split into {world} ranges (one per GPU), "
+                            "NCCL all-reduce of the 4 result doubles per step" if split else
+                            "1 GPU" if world == 1 else f"{world} independent fields (one per GPU)"),
         },
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": kern_name,
                      "flops_per_launch": flops,
+                     "flops_count": "F(k) = k^3/3 + k^2/2 + k/6 + k^2 per location, k = m_i + 1 "
+                                    "(Cholesky and two triangular solves)",
+                     "frac_with_adjoint_solves": (flops_adj / (kern_ms * 1e-3) / 1e12) / peak,
                      "peak_source": "FP64 DFMA-chain kernel measured in this run (vecchia_fp64_peak)"},
         "covariance": {"entries_per_call": cov_evals, "entries_per_s": cov_evals / (kern_ms * 1e-3),
                        "note": "off-diagonal covariance entries k(k-1)/2 per location, k = m_i + 1"},
         "hbm": {"gbs": hbm_gbs, "source": "ncu dram bytes per launch (profiles/traffic.json) / CUDA-event time"},
-        "e2e": {"value": world * n / (e2e_ms * 1e-3), "unit": "locations/s",
+        "e2e": {"value": job_locations / (e2e_ms * 1e-3), "unit": "locations/s",
                 "h2d_bytes_per_step": int(y_host.numel() * 8), "d2h_bytes_per_step": int(res_host.numel() * 8)},
         "gpu_launches": 2 * args.steps,
         "clocks": clk.summary(),
@@ -591,6 +756,9 @@ def main():
         line["forward"] = {"kernel": "vecchia_lik_kernel<false> (plain per-field forward)",
                            "value": n / (fwd_ms * 1e-3), "unit": "locations/s", "ms_per_call": fwd_ms,
                            "frac_of_fp64_peak": ff / (fwd_ms * 1e-3) / 1e12 / peak}
+    if not args.no_configs:
+        line["configs"] = run_configs(V, dev, peak)
+        line["nu_estimation"] = run_nu_steps(V, dev)
     if not args.no_batched:
         line["batched"] = run_batched(V, dev, peak, scale=args.batched_scale)
     if not args.no_m_sweep:
@@ -600,7 +768,7 @@ def main():
     if not args.no_predict:
         line["predict"] = run_predict(V, dev)
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(xy, y, theta, m, args.cpu_budget)
+        line["cpu_baseline"] = cpu_baseline(xy, y, theta, m, args.cpu_budget, plan.perm(), plan.neighbors())
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

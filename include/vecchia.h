@@ -25,9 +25,9 @@
  *   - A plan may be used by one stream at a time: calls that share a plan must be
  *     ordered on the same stream (or externally synchronised).
  *   - Failures found on the GPU (a conditional block that is not positive
- *     definite) cannot be returned by the asynchronous call itself: the affected
- *     outputs become NaN and vecchia_last_error_location() reports the first
- *     failing ordered location.
+ *     definite, a non-finite value in y) cannot be returned by the asynchronous call
+ *     itself: the affected outputs become NaN and vecchia_last_error_location()
+ *     reports the first failing ordered location and the kind of failure.
  */
 #ifndef VECCHIA_H
 #define VECCHIA_H
@@ -181,6 +181,21 @@ int vecchia_loglik_terms(vecchia_plan_t plan, const double* y_dev, const double 
                          int want_grad, double* terms_dev, void* stream);
 
 /*
+ * vecchia_loglik_range — the part of l (and, if want_grad, of its gradient) contributed by
+ * the ordered locations i0 <= i < i1: Algorithm 1's sum restricted to a contiguous range
+ * of its n independent terms (Sec. V-B), the unit by which the likelihood is split
+ * across GPUs.  For disjoint ranges covering [0, n) the outputs add up to those of
+ * vecchia_loglik / vecchia_loglik_grad (every output is linear in the per-location sums).
+ *   i0, i1  : 0 <= i0 <= i1 <= n; i0 == i1 writes zeros.
+ *   out_dev : 1 (want_grad == 0) or 4 doubles on the device: the range's {l[, dl/dsigma2,
+ *             dl/dbeta, dl/dtau2]}.
+ * Same asynchrony and errors as vecchia_loglik, plus EINVAL for a range outside [0, n];
+ * vecchia_last_error_location reports the first failing location within the range.
+ */
+int vecchia_loglik_range(vecchia_plan_t plan, const double* y_dev, const double theta[4], int64_t i0, int64_t i1,
+                         int want_grad, double* out_dev, void* stream);
+
+/*
  * vecchia_matern — the covariance of Eq. (2) and its beta-derivative, evaluated by the
  * same device code the likelihood kernels use.
  *   d_dev        : count distances (>= 0) on the device.
@@ -212,6 +227,23 @@ int vecchia_covariance(int kernel, const double* d_dev, int64_t count, const dou
  * Asynchronous on `stream`.  Errors: EINVAL (count < 0, or NULL buffers), ECUDA.
  */
 int vecchia_pivot_reciprocal(const double* d_dev, int64_t count, double* out_dev, void* stream);
+
+/*
+ * vecchia_mul_by_positive — the product the full-warp likelihood kernels use to scale an
+ * elimination column by its pivot reciprocal (Algorithm 1's factorisation step, written
+ * as L D L^T), exposed so its exactness can be checked.  It uses no FP64 instruction:
+ * the 106-bit mantissa product is formed from 32-bit integer limbs and rounded to
+ * nearest, ties to even.
+ *   a_dev, b_dev : count doubles each on the device; b must be a positive normal double
+ *                  (a pivot reciprocal), a any finite double.
+ *   out_dev      : count doubles on the device: a * b, bit-identical to the FP64 product
+ *                  whenever the exact product is finite with magnitude at least 2^-1022;
+ *                  an exact product below 2^-1022 in magnitude (or a zero or subnormal a)
+ *                  gives a zero of a's sign, one that rounds beyond the largest double an
+ *                  infinity.
+ * Asynchronous on `stream`.  Errors: EINVAL (count < 0, or NULL buffers), ECUDA.
+ */
+int vecchia_mul_by_positive(const double* a_dev, const double* b_dev, int64_t count, double* out_dev, void* stream);
 
 /*
  * vecchia_batched_prepare — builds the covariance tables the batched call may use, one per
@@ -255,7 +287,7 @@ int vecchia_loglik_batched(const vecchia_plan_t* plans, const double* const* y_d
  * forbidden (for example inside a host allocator's callback, a memory-capped arena
  * that owns every device byte, or a runtime that must never trigger an allocation
  * while serving).  It has no counterpart in the paper.  It calls no cudaMalloc,
- * cudaFree or other allocating routine; its scratch (per-warp partial sums for at
+ * cudaFree or other allocating routine; its scratch (partial sums for launches of at
  * most 4096 warps, an error slot and one covariance table, about 190 KB) is a
  * file-scope __device__ array that every GPU loading the library keeps until the
  * process exits.  The launch is capped at 4096 warps; the kernel strides over the
@@ -268,9 +300,18 @@ int vecchia_loglik_batched(const vecchia_plan_t* plans, const double* const* y_d
  *   self_dev : n int32, ORIGINAL index of the i-th ordered location (= perm[i]).
  *   n, m     : 1 <= n <= 2^31 - 1, 1 <= m <= VECCHIA_MAX_M_WARP; otherwise EINVAL.
  *   theta    : host double[4] as for vecchia_loglik; out_dev: 1 double on the device.
+ * The kernel checks every entry of self_dev and the first m_i entries of each nbr_dev
+ * row against [0, n) before reading through it: an entry outside that range makes
+ * out_dev NaN (it is never used as an address).
  * Asynchronous on `stream`.  The first call on a device looks up the scratch array's
- * device address (cudaGetSymbolAddress); make that first call before any stream
- * capture.  Every call reuses the same scratch and rebuilds the covariance table in
+ * device address (cudaGetSymbolAddress); with lazy module loading (the CUDA default)
+ * that first call, or the first launch of this library's kernels on the device, is
+ * also when the driver loads the module and its __device__ arrays, which can allocate
+ * device memory.  So make the first call on each device outside any context that must
+ * not allocate, and before any stream capture.  The looked-up address is kept for the
+ * life of the process: a device reset (cudaDeviceReset) or a new primary context on the
+ * device invalidates it, and the library must not be called on that device afterwards.
+ * Every call reuses the same scratch and rebuilds the covariance table in
  * it, so calls that overlap on the GPU (different streams, or different host threads,
  * on one device) race and must be serialised by the caller.  A block that is not
  * positive definite makes out_dev NaN.  Errors: EINVAL, ECUDA.
@@ -325,8 +366,11 @@ int vecchia_predict(vecchia_plan_t plan, const double* xy_new_host, int64_t n_ne
 
 /*
  * vecchia_last_error_location — synchronises the stream of the plan's last call and
- * reports the first ordered location whose block was not positive definite in that
- * call (*loc = -1 if none).  Returns ENOTPD if there was one, else OK.
+ * reports the first ordered location whose term failed in that call (*loc = -1 if
+ * none).  Returns VECCHIA_ENOTPD if that location's block was not positive definite,
+ * VECCHIA_EINVAL if the block held a non-finite data value (y at the location or at one
+ * of its conditioning points: y_dev is not scanned up front, since the calls are
+ * asynchronous), else VECCHIA_OK.
  */
 int vecchia_last_error_location(vecchia_plan_t plan, int64_t* loc);
 

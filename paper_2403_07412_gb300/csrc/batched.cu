@@ -81,6 +81,7 @@ __device__ __forceinline__ void run_item(const FieldDesc& fd, int64_t tile, cons
   F.self = fd.self;
   F.n = fd.n;
   F.m = fd.m;
+  F.nidx = fd.n;
   const int K = fd.m + 1;
   const SchedSize S(K);
   const uint16_t* sched = reinterpret_cast<const uint16_t*>(smem + a.sched_off[fd.kidx]);
@@ -123,6 +124,12 @@ __global__ void __launch_bounds__(384) vecchia_batched_kernel(const BatchArgs a)
     const int64_t rel = (int64_t)item - fd.item_base;
     const int t = (int)(rel / fd.tiles);
     const int64_t tile = rel % fd.tiles;
+    if (kChecked && (t >= a.ntheta || tile >= fd.tiles || lo < 0 || lo >= a.nfields)) {
+      if (lane == 0) {  // a work item outside the layout: record it and skip it
+        atomicMin(a.errloc, err_code((int64_t)item, kErrIndex));
+      }
+      continue;
+    }
     const double* th = a.thetas + ((int64_t)fd.orig * a.ntheta + t) * 4;
     const double s2 = th[0], beta = th[1], nu = th[2], t2 = th[3];
     const double* tab = nullptr;
@@ -134,7 +141,7 @@ __global__ void __launch_bounds__(384) vecchia_batched_kernel(const BatchArgs a)
     if (!tab || !theta_valid) {
       if (lane == 0) {
         out[0] = out[1] = out[2] = out[3] = __longlong_as_double(0x7FF8000000000000LL);
-        atomicMin(a.errloc, 0ULL);
+        atomicMin(a.errloc, err_code(0, kErrData));
       }
       continue;
     }

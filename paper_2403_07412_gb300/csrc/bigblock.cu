@@ -37,6 +37,7 @@ struct BigArgs {
   const double* __restrict__ xyz;  // n x 3 unit vectors (sphere plans)
   int metric;                      // 0 plane, 1 sphere
   double radius;
+  int64_t i0, i1;                  // ordered locations [i0, i1) are evaluated
 };
 
 // Largest w with w(w+1)/2 <= e (e < 2^24).
@@ -165,10 +166,15 @@ __global__ void __launch_bounds__(kCtaThreadsMax) vecchia_big_kernel(const BigAr
     F.k2 = d2f_pair(F.k2d);
   }
   Accum acc;
-  for (int64_t i = blockIdx.x; i < a.n; i += gridDim.x) {
+  for (int64_t i = a.i0 + blockIdx.x; i < a.i1; i += gridDim.x) {
     const int mi = i < m ? (int)i : m;
     const int32_t* __restrict__ row = a.nbr + i * m;
-    const int js = a.self[i];
+    bool bad_idx = false;  // bounds-checked builds only: an index outside [0, n)
+    int js = a.self[i];
+    if (kChecked && (unsigned long long)(int64_t)js >= (unsigned long long)a.n) {
+      bad_idx = true;
+      js = 0;
+    }
     const double2 ps = xy2[js];
     // ---- gather (two slots per thread covers m <= 2 * kCtaThreads): centred,
     // 1/beta-scaled coordinates as float pairs, and data
@@ -178,7 +184,11 @@ __global__ void __launch_bounds__(kCtaThreadsMax) vecchia_big_kernel(const BigAr
       if (p < m) {
         double xv = 0.0, yv = 0.0, zv = 0.0, fv = 0.0;
         if (p < mi) {
-          const int j = row[p];
+          int j = row[p];
+          if (kChecked && (unsigned long long)(int64_t)j >= (unsigned long long)a.n) {
+            bad_idx = true;
+            j = 0;
+          }
           if constexpr (SPHERE) {
             xv = a.xyz[3 * j] - a.xyz[3 * js];
             yv = a.xyz[3 * j + 1] - a.xyz[3 * js + 1];
@@ -202,6 +212,7 @@ __global__ void __launch_bounds__(kCtaThreadsMax) vecchia_big_kernel(const BigAr
       if constexpr (SPHERE) CZ[m] = make_float2(0.0f, 0.0f);
       YV[m] = a.yf[js];
     }
+    if (kChecked) bad_idx = __syncthreads_or(bad_idx) != 0;
     __syncthreads();
     // ---- assemble
     for (int c = tid; c < K; c += NTH) {
@@ -236,7 +247,8 @@ __global__ void __launch_bounds__(kCtaThreadsMax) vecchia_big_kernel(const BigAr
     for (; ok && j + 2 < K; j += 2) ok = cta_columns<2>(A, TVs, K, j, tid, NTH);
     if (ok && j + 1 < K) ok = cta_columns<1>(A, TVs, K, j, tid, NTH);
     const double st = A[1], rr = A[2];
-    const bool good = ok && positive_finite(st);
+    const bool pd = ok && positive_finite(st);  // a non-finite rr with pd: non-finite data
+    const bool good = pd && finite_bits(rr) && !bad_idx;
     const double nan = __longlong_as_double(0x7FF8000000000000LL);
     const double s = tc.sigma2 * st;
     const double inv_s = rcp_newton(s);
@@ -247,7 +259,7 @@ __global__ void __launch_bounds__(kCtaThreadsMax) vecchia_big_kernel(const BigAr
       acc.count += 1;
     } else {
       acc.Q.add(nan);
-      if (tid == 0) atomicMin(a.errloc, (unsigned long long)i);
+      if (tid == 0) atomicMin(a.errloc, err_code(i, bad_idx ? kErrIndex : (pd ? kErrData : kErrNotPD)));
     }
     const double li = good ? -0.5 * q - 0.5 * log(s) - 0.91893853320467274178 : nan;
     if (!GRAD) {
@@ -347,8 +359,10 @@ __global__ void __launch_bounds__(kCtaThreadsMax) vecchia_big_kernel(const BigAr
       acc.S += sS;
       acc.B += pB;
       acc.T += pT;
-    } else {
+    } else {  // every output of a failed term is NaN
       acc.S += nan;
+      acc.B += nan;
+      acc.T += nan;
     }
     __syncthreads();
   }

@@ -139,6 +139,10 @@ struct FieldView {
   const int32_t* __restrict__ self; // n
   int64_t n;
   int m;
+  // indices into xy / yf must lie in [0, nidx); checked before use when check_idx (a
+  // warp-uniform flag) or in a bounds-checked build
+  int64_t nidx = 0;
+  bool check_idx = false;
   // great-circle distances: unit vectors (n x 3, original order) and K2 = (2 r / len)^2,
   // with len the family's length scale, as a float pair and in FP64
   const double* __restrict__ xyz = nullptr;
@@ -349,7 +353,13 @@ __device__ __forceinline__ void process_location(int64_t i, bool active, const F
   double* __restrict__ TV = W.TV;
   const int mi = (i < m && !F.pmean) ? (int)i : m;
   const int32_t* __restrict__ row = F.nbr + i * m;
-  const int js = F.self[i];
+  const bool check = kChecked || F.check_idx;
+  bool bad_idx = false;
+  int js = F.self[i];
+  if (check && (unsigned long long)(int64_t)js >= (unsigned long long)F.nidx) {
+    bad_idx = true;
+    js = 0;
+  }
   const double2 ps = F.xy[js];
   // ---- gather: centred, 1/beta-scaled coordinates (as float pairs) and data
 #pragma unroll
@@ -358,7 +368,11 @@ __device__ __forceinline__ void process_location(int64_t i, bool active, const F
     if (p < m) {
       double xv = 0.0, yv = 0.0, zv = 0.0, fv = 0.0;
       if (p < mi) {
-        const int j = row[p];
+        int j = row[p];
+        if (check && (unsigned long long)(int64_t)j >= (unsigned long long)F.nidx) {
+          bad_idx = true;
+          j = 0;
+        }
         if constexpr (SPHERE) {  // unit-vector offsets; the length scale enters through K2
           xv = F.xyz[3 * j] - F.xyz[3 * js];
           yv = F.xyz[3 * j + 1] - F.xyz[3 * js + 1];
@@ -381,6 +395,11 @@ __device__ __forceinline__ void process_location(int64_t i, bool active, const F
     CY[m] = make_float2(0.0f, 0.0f);
     if constexpr (SPHERE) CZ[m] = make_float2(0.0f, 0.0f);
     YV[m] = F.yf[js];
+  }
+  if (check) {  // a bad index anywhere in the group fails the group's block
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned gmask = G == 32 ? 0xffffffffu : ((1u << G) - 1u) << (lane & ~(unsigned)(G - 1));
+    bad_idx = (__ballot_sync(0xffffffffu, bad_idx) & gmask) != 0u;
   }
   __syncwarp();
   // ---- assemble: diagonal, data border, then the correlation pairs
@@ -558,7 +577,10 @@ __device__ __forceinline__ void process_location(int64_t i, bool active, const F
   }
   const double st = A[1];  // s_i / sigma2
   const double rr = A[2];  // y_i - mu_i
-  const bool good = ok && positive_finite(st);
+  // The pivots and s_i depend on the covariance only, the residual on the data: a
+  // non-finite residual (with a positive definite block) means a non-finite y in B_i.
+  const bool pd = ok && positive_finite(st);
+  const bool good = pd && finite_bits(rr) && !bad_idx;
   const double nan = __longlong_as_double(0x7FF8000000000000LL);
   const double s = tc.sigma2 * st;
   const double inv_s = rcp_newton(s);
@@ -570,14 +592,16 @@ __device__ __forceinline__ void process_location(int64_t i, bool active, const F
       acc.count += 1;
     } else {
       acc.Q.add(nan);
-      if (sub == 0 && !F.pmean) atomicMin(errloc, (unsigned long long)i);
+      if (sub == 0 && !F.pmean) atomicMin(errloc, err_code(i, bad_idx ? kErrIndex : (pd ? kErrData : kErrNotPD)));
     }
     if (F.pmean && sub == 0) {
       // y_i = 0 here, so rr = -mu; a variance of 0 (prediction at an observed point
-      // without nugget) is valid, so only a failed neighbour factorisation gives NaN
-      F.pmean[i] = ok ? -rr : nan;
-      if (F.pvar) F.pvar[i] = ok ? fmax(s, 0.0) : nan;
-      if (!ok) atomicMin(errloc, (unsigned long long)i);
+      // without nugget) is valid, so only a failed neighbour factorisation, a bad index
+      // or non-finite data gives NaN
+      const bool pok = ok && !bad_idx && finite_bits(rr);
+      F.pmean[i] = pok ? -rr : nan;
+      if (F.pvar) F.pvar[i] = pok ? fmax(s, 0.0) : nan;
+      if (!pok) atomicMin(errloc, err_code(i, bad_idx ? kErrIndex : (ok ? kErrData : kErrNotPD)));
     }
   }
   // per-location terms (test and inspection path) pay for their own log
@@ -691,8 +715,10 @@ __device__ __forceinline__ void process_location(int64_t i, bool active, const F
       acc.S += sS;
       acc.B += pB;
       acc.T += pT;
-    } else {
+    } else {  // every output of a failed term is NaN
       acc.S += nan;
+      acc.B += nan;
+      acc.T += nan;
     }
   }
   __syncwarp();

@@ -51,15 +51,10 @@ struct Plan {
   int64_t* h_perm = nullptr;  // n, host copy of the ordering
   int32_t* d_inv = nullptr;   // n, ordered position of each original index
   // reusable scratch
-  double* d_partial = nullptr;  // per-warp partial sums
+  double* d_partial = nullptr;  // per-CTA partial sums
   int64_t partial_cap = 0;
   unsigned long long* d_errloc = nullptr;  // first failing location (ULLONG_MAX = none)
   cudaStream_t last_stream = nullptr;
-  // covariance tables, cached by nu
-  static constexpr int kCache = 4;
-  double cache_nu[kCache] = {0, 0, 0, 0};
-  double* cache_tab[kCache] = {nullptr, nullptr, nullptr, nullptr};
-  int cache_next = 0;
 };
 
 // ------------------------------------------------------------------ device helpers
@@ -113,9 +108,10 @@ __device__ __forceinline__ double rcp_fixed(double d) {
 }
 
 // a b for b a positive normal double (a pivot reciprocal), by integer arithmetic with
-// round-to-nearest-even: equal to the FP64 product whenever that is normal.  The 106-bit
-// mantissa product is formed from 32-bit limbs; a zero or subnormal a, or a product
-// below the normal range, gives a signed zero, and one above it an infinity.
+// round-to-nearest-even: equal to the FP64 product whenever the exact product is finite
+// and at least 2^-1022 in magnitude.  The 106-bit mantissa product is formed from 32-bit
+// limbs; a zero or subnormal a, or an exact product below 2^-1022, gives a zero of a's
+// sign, and one that rounds beyond the largest double an infinity.
 __device__ __forceinline__ double mul_by_positive(double a, double b) {
   const unsigned long long A = (unsigned long long)__double_as_longlong(a);
   const unsigned long long B = (unsigned long long)__double_as_longlong(b);
@@ -153,6 +149,11 @@ __device__ __forceinline__ bool positive_finite(double d) {
   return b > 0 && b < 0x7FF0000000000000LL;
 }
 
+// True iff d is finite (not an infinity or NaN), decided on the bit pattern.
+__device__ __forceinline__ bool finite_bits(double d) {
+  return (__double_as_longlong(d) & 0x7FF0000000000000LL) != 0x7FF0000000000000LL;
+}
+
 struct Neumaier {
   double s = 0.0, c = 0.0;
   __device__ __forceinline__ void add(double x) {
@@ -160,8 +161,38 @@ struct Neumaier {
     if (fabs(s) >= fabs(x)) c += (s - t) + x; else c += (x - t) + s;
     s = t;
   }
+  // Adds another compensated sum (its sum and compensation).
+  __device__ __forceinline__ void merge(double s2, double c2) {
+    const double t = s + s2;
+    const double e = fabs(s) >= fabs(s2) ? (s - t) + s2 : (s2 - t) + s;
+    s = t;
+    c = (c + c2) + e;
+  }
   __device__ __forceinline__ double value() const { return s + c; }
 };
+
+// ------------------------------------------------------------------ error slot
+// A call's error slot holds the smallest code (location << 2 | kind) written by any
+// failing location, so the first failing ordered location wins and, at one location, the
+// lower kind.  All ones means no failure.
+constexpr unsigned kErrIndex = 0;  // a conditioning-set or location index outside [0, n)
+constexpr unsigned kErrData = 1;   // a non-finite data value in the block
+constexpr unsigned kErrNotPD = 2;  // a block that is not positive definite
+__host__ __device__ __forceinline__ unsigned long long err_code(int64_t i, unsigned kind) {
+  return ((unsigned long long)i << 2) | kind;
+}
+
+// Bounds-checked build (-DVECCHIA_CHECKED): every index the kernels read through (the
+// conditioning sets, the location itself, the batched work items) is checked against
+// its range before use; a bad one is recorded in the error slot (kErrIndex) and replaced
+// by a valid index, and the affected outputs become NaN.  No trap, no fault.  Without the
+// flag the single-field kernels check the caller-supplied index arrays only where the
+// caller, not a plan, provided them (the allocation-free entry point).
+#ifdef VECCHIA_CHECKED
+constexpr bool kChecked = true;
+#else
+constexpr bool kChecked = false;
+#endif
 
 }  // namespace vecchia
 

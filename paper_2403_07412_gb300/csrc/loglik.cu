@@ -19,6 +19,24 @@ namespace vecchia {
 
 int get_matern_table(double nu, cudaStream_t stream, const double** out);
 int get_cov_table(int family, double nu, cudaStream_t stream, const double** out);
+void cov_table_used(const double* tab, cudaStream_t stream);
+
+// A covariance table taken from the cache for one call: when the call's scope ends (after
+// its launches, or on an early error return) the use is recorded on the stream.
+struct TablePin {
+  const double* tab = nullptr;
+  cudaStream_t stream = nullptr;
+  TablePin() = default;
+  TablePin(const TablePin&) = delete;
+  TablePin& operator=(const TablePin&) = delete;
+  int get(int family, double nu, cudaStream_t s) {
+    stream = s;
+    return get_cov_table(family, nu, s, &tab);
+  }
+  ~TablePin() {
+    if (tab) cov_table_used(tab, stream);
+  }
+};
 
 struct BigArgs {
   const double* __restrict__ xy;
@@ -36,6 +54,7 @@ struct BigArgs {
   const double* __restrict__ xyz;  // n x 3 unit vectors (sphere plans)
   int metric;                      // 0 plane, 1 sphere
   double radius;
+  int64_t i0, i1;                  // ordered locations [i0, i1) are evaluated
 };
 int big_config(int K, bool grad, int* blocks, int* threads, int* smem, bool sphere);
 void launch_big(bool grad, int blocks, int threads, int smem, const BigArgs& a, cudaStream_t s);
@@ -61,6 +80,9 @@ struct LikArgs {
   double radius = 1.0;
   double* pmean = nullptr;           // prediction outputs (n), see FieldView
   double* pvar = nullptr;
+  int64_t i0 = 0, i1 = 0;            // ordered locations [i0, i1) are evaluated
+  int64_t n_index = 0;               // entries of xy / yf (0: n)
+  bool check_idx = false;            // check nbr / self entries against [0, n_index)
 };
 
 // Shared-memory layout for block size K (= m + 1), G lanes per location (32/G locations
@@ -103,6 +125,8 @@ __global__ void __launch_bounds__(384) vecchia_lik_kernel(const LikArgs a) {
   F.self = a.self;
   F.n = a.n;
   F.m = a.m;
+  F.nidx = a.n_index > 0 ? a.n_index : a.n;
+  F.check_idx = a.check_idx;
   F.pmean = a.pmean;
   F.pvar = a.pvar;
   if constexpr (SPHERE) {
@@ -116,38 +140,55 @@ __global__ void __launch_bounds__(384) vecchia_lik_kernel(const LikArgs a) {
   const int64_t nw = (int64_t)gridDim.x * W;
   const bool terms_mode = a.terms != nullptr;
   Accum acc;
-  for (int64_t base = gw * NL; base < a.n; base += nw * NL) {
+  for (int64_t base = a.i0 + gw * NL; base < a.i1; base += nw * NL) {
     const int64_t i = base + grp;
-    const bool active = i < a.n;
+    const bool active = i < a.i1;
     const int64_t ii = active ? i : base;
     double* trow = terms_mode ? a.terms + ii * (GRAD ? 4 : 1) : nullptr;
     process_location<GRAD, G, SPHERE>(ii, active, F, L.S, sched, pairs, area, a.tab, mc, tc, acc, terms_mode, trow,
                               a.errloc, sub);
   }
-  write_partial<G>(acc, a.partial + gw * 4, lane);
+  // The CTA's warps' sums are combined in warp order (compensated), one record per CTA.
+  __shared__ double wpart[12][4];
+  write_partial<G>(acc, wpart[wib], lane);
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    Neumaier c;
+    for (int w = 0; w < W; ++w) c.add(wpart[w][threadIdx.x]);
+    a.partial[(int64_t)blockIdx.x * 4 + threadIdx.x] = c.value();
+  }
 }
 
-// Deterministic reduction of the per-warp partials (fixed order, Neumaier).
-// Partials: [sum l_i, sum 1/2(r^2/s-1), sum beta pair sums, sum w^T g]; dbeta_div is 1
+// Deterministic reduction of the per-CTA records: warp k sums column k, each lane a
+// strided subset (compensated), then the lanes' (sum, compensation) pairs are merged by a
+// fixed shuffle tree, so the result depends only on the number of records.
+// Records: [sum l_i, sum 1/2(r^2/s-1), sum beta pair sums, sum w^T g]; dbeta_div is 1
 // (Matérn) or alpha (power exponential).
-__global__ void vecchia_finalize_kernel(const double* __restrict__ partial, int64_t nw, double sigma2,
-                                        double beta, double tau2, double dbeta_div, int want_grad, double* out) {
-  if (threadIdx.x >= 4) return;
-  const int k = threadIdx.x;
+__global__ void __launch_bounds__(128) vecchia_finalize_kernel(const double* __restrict__ partial, int64_t np,
+                                                               double sigma2, double beta, double tau2,
+                                                               double dbeta_div, int want_grad, double* out) {
+  const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
   Neumaier acc;
-  for (int64_t w = 0; w < nw; ++w) acc.add(partial[w * 4 + k]);
-  const double v = acc.value();
-  if (!want_grad) {
-    if (k == 0) out[0] = v;
-    return;
+  for (int64_t w = lane; w < np; w += 32) acc.add(partial[w * 4 + k]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double s2 = __shfl_down_sync(0xffffffffu, acc.s, o);
+    const double c2 = __shfl_down_sync(0xffffffffu, acc.c, o);
+    acc.merge(s2, c2);
   }
   __shared__ double sv[4];
-  sv[k] = v;
-  __syncwarp(0xFu);
-  if (k == 0) out[0] = sv[0];
-  if (k == 1) out[1] = (sv[1] - tau2 * sv[3]) / sigma2;
-  if (k == 2) out[2] = -2.0 * sigma2 / (beta * dbeta_div) * sv[2];
-  if (k == 3) out[3] = sv[3];
+  if (lane == 0) sv[k] = acc.value();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (!want_grad) {
+      out[0] = sv[0];
+      return;
+    }
+    out[0] = sv[0];
+    out[1] = (sv[1] - tau2 * sv[3]) / sigma2;
+    out[2] = -2.0 * sigma2 / (beta * dbeta_div) * sv[2];
+    out[3] = sv[3];
+  }
 }
 
 // ------------------------------------------------------------------ launch
@@ -290,7 +331,7 @@ int lanes_for(int K, bool grad) {
 
 namespace {
 int launch_with(Plan* p, const double* y_dev, const double* theta, bool grad, const LaunchCfg& cfg,
-                double* out_dev, double* terms_dev, cudaStream_t stream) {
+                double* out_dev, double* terms_dev, cudaStream_t stream, int64_t i0, int64_t i1) {
   const int64_t nw = (int64_t)cfg.blocks * cfg.W;
   if (p->partial_cap < nw * 4) {
     if (p->d_partial) cudaFree(p->d_partial);
@@ -299,9 +340,10 @@ int launch_with(Plan* p, const double* y_dev, const double* theta, bool grad, co
     if (cudaMalloc(&p->d_partial, sizeof(double) * nw * 4) != cudaSuccess) return VECCHIA_ENOMEM;
     p->partial_cap = nw * 4;
   }
-  const double* tab = nullptr;
-  int rc = get_cov_table(p->family, theta[2], stream, &tab);
+  TablePin pin;
+  int rc = pin.get(p->family, theta[2], stream);
   if (rc) return rc;
+  const double* tab = pin.tab;
   VECCHIA_CUDA_TRY(cudaMemsetAsync(p->d_errloc, 0xFF, sizeof(unsigned long long), stream));
   LikArgs a;
   a.xy = p->d_xy;
@@ -322,12 +364,14 @@ int launch_with(Plan* p, const double* y_dev, const double* theta, bool grad, co
   a.xyz = p->d_xyz;
   a.metric = p->metric;
   a.radius = p->radius;
+  a.i0 = i0;
+  a.i1 = i1;
   launch_lik(cfg, grad, a, stream);
   VECCHIA_CUDA_TRY(cudaGetLastError());
   if (out_dev) {
     const double dbeta_div = p->family == kFamilyPowExp ? theta[2] : 1.0;
-    vecchia_finalize_kernel<<<1, 32, 0, stream>>>(p->d_partial, nw, theta[0], theta[1], theta[3], dbeta_div,
-                                                  grad ? 1 : 0, out_dev);
+    vecchia_finalize_kernel<<<1, 128, 0, stream>>>(p->d_partial, cfg.blocks, theta[0], theta[1], theta[3], dbeta_div,
+                                                   grad ? 1 : 0, out_dev);
     VECCHIA_CUDA_TRY(cudaGetLastError());
   }
   p->last_stream = stream;
@@ -337,7 +381,7 @@ int launch_with(Plan* p, const double* y_dev, const double* theta, bool grad, co
 
 // Blocks beyond the warp kernels' size: one CTA per location (bigblock.cu).
 static int launch_big_loglik(Plan* p, const double* y_dev, const double* theta, bool grad, double* out_dev,
-                             double* terms_dev, cudaStream_t stream) {
+                             double* terms_dev, cudaStream_t stream, int64_t i0, int64_t i1) {
   int blocks = 0, threads = 0, smem = 0;
   int rc = big_config(p->m + 1, grad, &blocks, &threads, &smem, p->metric == 1);
   if (rc) return rc;
@@ -348,9 +392,10 @@ static int launch_big_loglik(Plan* p, const double* y_dev, const double* theta, 
     if (cudaMalloc(&p->d_partial, sizeof(double) * blocks * 4) != cudaSuccess) return VECCHIA_ENOMEM;
     p->partial_cap = (int64_t)blocks * 4;
   }
-  const double* tab = nullptr;
-  rc = get_cov_table(p->family, theta[2], stream, &tab);
+  TablePin pin;
+  rc = pin.get(p->family, theta[2], stream);
   if (rc) return rc;
+  const double* tab = pin.tab;
   VECCHIA_CUDA_TRY(cudaMemsetAsync(p->d_errloc, 0xFF, sizeof(unsigned long long), stream));
   BigArgs a;
   a.xy = p->d_xy;
@@ -371,26 +416,37 @@ static int launch_big_loglik(Plan* p, const double* y_dev, const double* theta, 
   a.xyz = p->d_xyz;
   a.metric = p->metric;
   a.radius = p->radius;
+  a.i0 = i0;
+  a.i1 = i1;
   launch_big(grad, blocks, threads, smem, a, stream);
   VECCHIA_CUDA_TRY(cudaGetLastError());
   if (out_dev) {
     const double dbeta_div = p->family == kFamilyPowExp ? theta[2] : 1.0;
-    vecchia_finalize_kernel<<<1, 32, 0, stream>>>(p->d_partial, blocks, theta[0], theta[1], theta[3], dbeta_div,
-                                                  grad ? 1 : 0, out_dev);
+    vecchia_finalize_kernel<<<1, 128, 0, stream>>>(p->d_partial, blocks, theta[0], theta[1], theta[3], dbeta_div,
+                                                   grad ? 1 : 0, out_dev);
     VECCHIA_CUDA_TRY(cudaGetLastError());
   }
   p->last_stream = stream;
   return VECCHIA_OK;
 }
 
+// Ordered locations [i0, i1) (i1 < 0: all n).  An empty range writes zeros.
 int launch_loglik(Plan* p, const double* y_dev, const double* theta, bool grad, double* out_dev,
-                  double* terms_dev, cudaStream_t stream) {
+                  double* terms_dev, cudaStream_t stream, int64_t i0, int64_t i1) {
   if (!p || !y_dev || !theta_ok_family(theta, p->family) || (!out_dev && !terms_dev)) return VECCHIA_EINVAL;
-  if (p->m > kMaxMWarp) return launch_big_loglik(p, y_dev, theta, grad, out_dev, terms_dev, stream);
+  if (i1 < 0) i1 = p->n;
+  if (i0 < 0 || i0 > i1 || i1 > p->n) return VECCHIA_EINVAL;
+  if (i0 == i1) {
+    if (out_dev) VECCHIA_CUDA_TRY(cudaMemsetAsync(out_dev, 0, sizeof(double) * (grad ? 4 : 1), stream));
+    VECCHIA_CUDA_TRY(cudaMemsetAsync(p->d_errloc, 0xFF, sizeof(unsigned long long), stream));
+    p->last_stream = stream;
+    return VECCHIA_OK;
+  }
+  if (p->m > kMaxMWarp) return launch_big_loglik(p, y_dev, theta, grad, out_dev, terms_dev, stream, i0, i1);
   LaunchCfg cfg;
   int rc = pick_config(p->m + 1, grad, &cfg, p->metric == 1);
   if (rc) return rc;
-  return launch_with(p, y_dev, theta, grad, cfg, out_dev, terms_dev, stream);
+  return launch_with(p, y_dev, theta, grad, cfg, out_dev, terms_dev, stream, i0, i1);
 }
 
 int knn_predict(Plan* p, const double* xy_new_host, int64_t n_new, int32_t* d_nbr_new, std::vector<double>* xyz_new_out,
@@ -447,8 +503,9 @@ int predict(Plan* p, const double* xy_new_host, int64_t n_new, const double* y_d
     if (cudaMalloc(&p->d_partial, sizeof(double) * nw * 4) != cudaSuccess) rc = VECCHIA_ENOMEM;
     else p->partial_cap = nw * 4;
   }
-  const double* tab = nullptr;
-  if (!rc) rc = get_cov_table(p->family, theta[2], stream, &tab);
+  TablePin pin;
+  if (!rc) rc = pin.get(p->family, theta[2], stream);
+  const double* tab = pin.tab;
   if (!rc && cudaMemsetAsync(p->d_errloc, 0xFF, sizeof(unsigned long long), stream) != cudaSuccess) rc = VECCHIA_ECUDA;
   if (!rc) {
     LikArgs a;
@@ -472,6 +529,9 @@ int predict(Plan* p, const double* xy_new_host, int64_t n_new, const double* y_d
     a.radius = p->radius;
     a.pmean = mean_dev;
     a.pvar = var_dev;
+    a.i0 = 0;
+    a.i1 = n_new;
+    a.n_index = nt;
     launch_lik(cfg, false, a, stream);
     if (cudaGetLastError() != cudaSuccess) rc = VECCHIA_ECUDA;
   }
@@ -518,7 +578,7 @@ int autotune(Plan* p, const double* y_dev, const double* theta, bool grad, int* 
       float tmin = 1e30f;
       for (int rep = 0; rep < 3 && !rc; ++rep) {
         cudaEventRecord(e0, stream);
-        rc = launch_with(p, y_dev, theta, grad, cfg, out, nullptr, stream);
+        rc = launch_with(p, y_dev, theta, grad, cfg, out, nullptr, stream, 0, p->n);
         cudaEventRecord(e1, stream);
         if (cudaEventSynchronize(e1) != cudaSuccess) rc = VECCHIA_ECUDA;
         float ms = 0.f;
@@ -555,7 +615,25 @@ __global__ void pivot_reciprocal_kernel(const double* __restrict__ d, int64_t co
   }
 }
 
+// The column-scaling product of the full-warp kernels on its own.
+__global__ void mul_by_positive_kernel(const double* __restrict__ a, const double* __restrict__ b, int64_t count,
+                                       double* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = mul_by_positive(a[i], b[i]);
+}
+
 }  // namespace vecchia
+
+extern "C" int vecchia_mul_by_positive(const double* a_dev, const double* b_dev, int64_t count, double* out_dev,
+                                       void* stream) {
+  if (count < 0 || (count > 0 && (!a_dev || !b_dev || !out_dev))) return VECCHIA_EINVAL;
+  if (count == 0) return VECCHIA_OK;
+  const int64_t blocks = std::min<int64_t>((count + 255) / 256, 4096);
+  vecchia::mul_by_positive_kernel<<<(int)blocks, 256, 0, (cudaStream_t)stream>>>(a_dev, b_dev, count, out_dev);
+  VECCHIA_CUDA_TRY(cudaGetLastError());
+  return VECCHIA_OK;
+}
 
 extern "C" int vecchia_pivot_reciprocal(const double* d_dev, int64_t count, double* out_dev, void* stream) {
   if (count < 0 || (count > 0 && (!d_dev || !out_dev))) return VECCHIA_EINVAL;
@@ -622,7 +700,6 @@ extern "C" int vecchia_loglik_noalloc(const double* xy_dev, const double* y_dev,
   // it is capped to the warps the scratch can hold.
   const int max_blocks = kNoAllocWarps / cfg.W;
   if (cfg.blocks > max_blocks) cfg.blocks = max_blocks;
-  const int64_t nw = (int64_t)cfg.blocks * cfg.W;
   rc = launch_matern_table(theta[2], tab, s);
   if (rc) return rc;
   VECCHIA_CUDA_TRY(cudaMemsetAsync(errloc, 0xFF, sizeof(unsigned long long), s));
@@ -642,9 +719,12 @@ extern "C" int vecchia_loglik_noalloc(const double* xy_dev, const double* y_dev,
   a.partial = partial;
   a.terms = nullptr;
   a.errloc = errloc;
+  a.i0 = 0;
+  a.i1 = n;
+  a.check_idx = true;  // caller-supplied index arrays: a bad entry fails its block, never reads out of bounds
   launch_lik(cfg, false, a, s);
   VECCHIA_CUDA_TRY(cudaGetLastError());
-  vecchia_finalize_kernel<<<1, 32, 0, s>>>(partial, nw, theta[0], theta[1], theta[3], 1.0, 0, out_dev);
+  vecchia_finalize_kernel<<<1, 128, 0, s>>>(partial, cfg.blocks, theta[0], theta[1], theta[3], 1.0, 0, out_dev);
   VECCHIA_CUDA_TRY(cudaGetLastError());
   return VECCHIA_OK;
 }

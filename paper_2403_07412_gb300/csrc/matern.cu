@@ -22,7 +22,15 @@
 
 namespace vecchia {
 
-__device__ double quad_I(double u, double nu) {
+// I(u) by the trapezoidal rule, computed by a whole warp: lane l takes nodes k = k0 + l
+// of each chunk of 32 on either side of the peak; a side ends after the first chunk that
+// reaches a node below e^-45 of the peak (the log-integrand is concave, so the tail only
+// falls from there).  Each lane keeps a compensated sum; the lanes' sums are merged by a
+// fixed shuffle tree and lane 0's result is returned on every lane.  (One FP64
+// instruction costs a warp as much with 1 lane active as with 32, so a single thread's
+// serial loop would take 32 times longer.)  All 32 lanes must call it together.
+__device__ double quad_I_warp(double u, double nu) {
+  const int lane = threadIdx.x & 31;
   const double a = 0.25 * u;
   const double et = 0.5 * (nu + sqrt(nu * nu + 4.0 * a));  // e^tau at the peak
   const double tc = log(et);
@@ -31,21 +39,30 @@ __device__ double quad_I(double u, double nu) {
   const double lpeak = nu * tc - et - a / et;
   Neumaier acc;
   for (int side = 0; side < 2; ++side) {
-    for (int k = side; k < 200000; ++k) {
+    for (int k0 = side; k0 < 200000; k0 += 32) {
+      const int k = k0 + lane;
       const double tau = side == 0 ? tc + k * h : tc - k * h;
       const double e = exp(tau);
       const double lv = nu * tau - e - a / e;
       acc.add(exp(lv - lpeak));
-      if (lv - lpeak < -45.0 && k > 3) break;
+      if (__any_sync(0xffffffffu, lv - lpeak < -45.0 && k > 3)) break;
     }
   }
-  return acc.value() * h * exp(lpeak);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double s2 = __shfl_down_sync(0xffffffffu, acc.s, o);
+    const double c2 = __shfl_down_sync(0xffffffffu, acc.c, o);
+    acc.merge(s2, c2);
+  }
+  return __shfl_sync(0xffffffffu, acc.value(), 0) * h * exp(lpeak);
 }
 
-// One thread: I(0) and the small-u expansion constants (family Matérn), or the
-// exponent (power exponential).
+// One warp: I(0) and the small-u expansion constants (family Matérn), or the exponent
+// (power exponential).
 __global__ void matern_const_kernel(double nu, int family, double* tab) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (blockIdx.x != 0 || threadIdx.x >= 32) return;
+  const double I0 = family == kFamilyPowExp ? 1.0 : quad_I_warp(0.0, nu);
+  if (threadIdx.x != 0) return;
   double* c = tab + 2 * kIntWords * kNInt;
   if (family == kFamilyPowExp) {
     c[0] = __longlong_as_double(3LL);
@@ -68,12 +85,12 @@ __global__ void matern_const_kernel(double nu, int family, double* tab) {
     c[4] = 1.0 / tgamma(1.0 + nu);
     c[5] = 0.25 / tgamma(2.0 + nu);
   }
-  c[6] = quad_I(0.0, nu);
+  c[6] = I0;
   c[7] = 0.0;
 }
 
-// One block of 32 threads per interval.  Node values: the Matérn quadrature, or the
-// power exponential exp(-u^(alpha/2)) (u = (d / beta^(1/alpha))^2) evaluated directly.
+// One block per interval, a warp per Chebyshev node.  Node values: the Matérn quadrature,
+// or the power exponential exp(-u^(alpha/2)) (u = (d / beta^(1/alpha))^2) evaluated directly.
 // One interval's coefficients in the layout of matern.cuh: c0 in FP64; c1..c4 and
 // 3 c3 as float pairs (hi = nearest float, lo = nearest float to the rest); c5..c8,
 // 5 c5, 6 c6 as floats; all floats scaled by 2^S, |max(c1..c4)| 2^S in [1/2, 1), so
@@ -108,7 +125,10 @@ __device__ void write_interval(const double* mono, float* w) {
   w[19] = (float)(6.0 * c[6]);
 }
 
-__global__ void matern_fit_kernel(double nu, int family, double* tab) {
+// One CTA of kFitThreads (a warp per node) per interval.
+constexpr int kFitThreads = 32 * (kDeg + 1);
+
+__global__ void __launch_bounds__(kFitThreads) matern_fit_kernel(double nu, int family, double* tab) {
   constexpr int N = kDeg + 1;
   __shared__ double f[N], cheb[N], mono[N], tm[N][N];
   const int idx = blockIdx.x;
@@ -119,10 +139,12 @@ __global__ void matern_fit_kernel(double nu, int family, double* tab) {
   const double scale = ldexp(1.0, e);
   const double mid = scale * (1.0 + (2.0 * j + 1.0) / (2.0 * (1 << kSub)));
   const double hw = scale / (2.0 * (1 << kSub));
-  if (tid < N) {
-    const double tn = cospi((tid + 0.5) / N);
+  {  // node w = warp w: the first-kind Chebyshev point cos(pi (w + 1/2) / N)
+    const int w = tid >> 5;
+    const double tn = cospi((w + 0.5) / N);
     const double u = mid + hw * tn;
-    f[tid] = family == kFamilyPowExp ? exp(-exp(0.5 * nu * log(u))) : quad_I(u, nu) / I0;
+    const double v = family == kFamilyPowExp ? exp(-exp(0.5 * nu * log(u))) : quad_I_warp(u, nu) / I0;
+    if ((tid & 31) == 0) f[w] = v;
   }
   if (tid == 0) {
     // Monomial coefficients of T_0..T_kDeg (exact small integers).
@@ -151,23 +173,38 @@ __global__ void matern_fit_kernel(double nu, int family, double* tab) {
 }
 
 // ------------------------------------------------------------------ table cache
+// Tables are cached per (device, family, nu), at most kMaxTables per process; a call that
+// needs a table not in the cache builds it on its own stream.  Every launch that reads a
+// table records a use event on its stream afterwards (cov_table_used; one event per
+// stream that used the table).  When the cache is full, the least recently used table
+// that no call is between look-up and launch of is rebuilt in place: the building stream
+// first waits on that table's use events, so the new contents are written only after
+// every earlier reader has finished.  Nothing synchronises the device or frees memory.
 namespace {
+struct TableUse {
+  cudaStream_t stream;
+  cudaEvent_t done;
+};
 struct TableEntry {
   int device = -1;
   int family = 0;
   double nu = 0.0;
   double* d_tab = nullptr;
-  cudaEvent_t ready = nullptr;
+  cudaEvent_t ready = nullptr;  // recorded after the build
+  std::vector<TableUse> uses;   // recorded after each launch that read the table
+  int pending = 0;              // calls between get_cov_table and cov_table_used
   unsigned long long last_use = 0;
 };
 std::mutex g_mu;
 std::vector<TableEntry> g_tables;
 unsigned long long g_clock = 0;
-constexpr size_t kMaxTables = 16;
+constexpr size_t kMaxTables = 32;
+constexpr size_t kMaxUseStreams = 8;
 }  // namespace
 
 // Returns (building on `stream` if needed) the device table for (family, nu) on the
-// current device.
+// current device, and makes `stream` wait until it is built.  The caller launches its
+// kernels and then calls cov_table_used(table, stream).
 int get_cov_table(int family, double nu, cudaStream_t stream, const double** out) {
   int dev = 0;
   VECCHIA_CUDA_TRY(cudaGetDevice(&dev));
@@ -176,42 +213,72 @@ int get_cov_table(int family, double nu, cudaStream_t stream, const double** out
     if (t.device == dev && t.family == family && t.nu == nu) {
       VECCHIA_CUDA_TRY(cudaStreamWaitEvent(stream, t.ready, 0));
       t.last_use = ++g_clock;
+      t.pending += 1;
       *out = t.d_tab;
       return VECCHIA_OK;
     }
   }
-  double* d = nullptr;
-  if (cudaMalloc(&d, kTableBytes) != cudaSuccess) return VECCHIA_ENOMEM;
-  cudaEvent_t ev;
-  if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
-    cudaFree(d);
-    return VECCHIA_ECUDA;
-  }
   TableEntry* slot = nullptr;
-  if (g_tables.size() < kMaxTables) {
+  TableEntry* victim = nullptr;
+  for (auto& t : g_tables)  // least recently used table of this device not pinned by a call
+    if (t.device == dev && t.pending == 0 && (!victim || t.last_use < victim->last_use)) victim = &t;
+  if (g_tables.size() >= kMaxTables && victim) {
+    // Rebuild in place once every earlier reader of the old contents has finished.
+    for (const TableUse& u : victim->uses) {
+      VECCHIA_CUDA_TRY(cudaStreamWaitEvent(stream, u.done, 0));
+      cudaEventDestroy(u.done);
+    }
+    victim->uses.clear();
+    slot = victim;
+  } else {
+    double* d = nullptr;
+    if (cudaMalloc(&d, kTableBytes) != cudaSuccess) return VECCHIA_ENOMEM;
+    cudaEvent_t ev;
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+      cudaFree(d);
+      return VECCHIA_ECUDA;
+    }
     g_tables.emplace_back();
     slot = &g_tables.back();
-  } else {
-    // Evict the least recently used table once no kernel can still be reading it.
-    slot = &*std::min_element(g_tables.begin(), g_tables.end(),
-                              [](const TableEntry& a, const TableEntry& b) { return a.last_use < b.last_use; });
-    cudaDeviceSynchronize();
-    cudaFree(slot->d_tab);
-    cudaEventDestroy(slot->ready);
-    *slot = TableEntry();
+    slot->d_tab = d;
+    slot->ready = ev;
   }
-  matern_const_kernel<<<1, 32, 0, stream>>>(nu, family, d);
-  matern_fit_kernel<<<kNInt, 32, 0, stream>>>(nu, family, d);
+  matern_const_kernel<<<1, 32, 0, stream>>>(nu, family, slot->d_tab);
+  matern_fit_kernel<<<kNInt, kFitThreads, 0, stream>>>(nu, family, slot->d_tab);
   VECCHIA_CUDA_TRY(cudaGetLastError());
-  VECCHIA_CUDA_TRY(cudaEventRecord(ev, stream));
+  VECCHIA_CUDA_TRY(cudaEventRecord(slot->ready, stream));
   slot->device = dev;
   slot->family = family;
   slot->nu = nu;
-  slot->d_tab = d;
-  slot->ready = ev;
+  slot->pending = 1;
   slot->last_use = ++g_clock;
-  *out = d;
+  *out = slot->d_tab;
   return VECCHIA_OK;
+}
+
+// Records that the kernels enqueued on `stream` so far have read `tab` (from
+// get_cov_table), and releases the call's pin on it.
+void cov_table_used(const double* tab, cudaStream_t stream) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  for (auto& t : g_tables) {
+    if (t.d_tab != tab) continue;
+    if (t.pending > 0) t.pending -= 1;
+    for (TableUse& u : t.uses)
+      if (u.stream == stream) {
+        cudaEventRecord(u.done, stream);
+        return;
+      }
+    if (t.uses.size() >= kMaxUseStreams) {  // fold the oldest stream's use into this one
+      cudaStreamWaitEvent(stream, t.uses.front().done, 0);
+      cudaEventDestroy(t.uses.front().done);
+      t.uses.erase(t.uses.begin());
+    }
+    cudaEvent_t ev;
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return;
+    cudaEventRecord(ev, stream);
+    t.uses.push_back({stream, ev});
+    return;
+  }
 }
 
 int get_matern_table(double nu, cudaStream_t stream, const double** out) {
@@ -222,7 +289,7 @@ int get_matern_table(double nu, cudaStream_t stream, const double** out) {
 // 16-byte aligned) on `stream`, without touching the cache.
 int launch_matern_table(double nu, double* tab, cudaStream_t stream) {
   matern_const_kernel<<<1, 32, 0, stream>>>(nu, kFamilyMatern, tab);
-  matern_fit_kernel<<<kNInt, 32, 0, stream>>>(nu, kFamilyMatern, tab);
+  matern_fit_kernel<<<kNInt, kFitThreads, 0, stream>>>(nu, kFamilyMatern, tab);
   VECCHIA_CUDA_TRY(cudaGetLastError());
   return VECCHIA_OK;
 }
@@ -270,6 +337,7 @@ static int covariance(int family, const double* d_dev, int64_t count, const doub
   const int64_t blocks = std::min<int64_t>((count + 255) / 256, 4096);
   matern_eval_kernel<<<(int)blocks, 256, 0, s>>>(d_dev, count, theta[0], theta[1], family, tab, c_dev,
                                                  dcdbeta_dev);
+  cov_table_used(tab, s);
   VECCHIA_CUDA_TRY(cudaGetLastError());
   return VECCHIA_OK;
 }

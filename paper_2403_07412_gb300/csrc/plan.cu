@@ -636,7 +636,7 @@ static void plan_free(Plan* p) {
 }
 
 int launch_loglik(Plan* p, const double* y_dev, const double* theta, bool grad, double* out_dev,
-                  double* terms_dev, cudaStream_t stream);
+                  double* terms_dev, cudaStream_t stream, int64_t i0, int64_t i1);
 int predict(Plan* p, const double* xy_new_host, int64_t n_new, const double* y_dev, const double* theta,
             double* mean_dev, double* var_dev, int32_t* nbr_host, cudaStream_t stream);
 void forget_plan_in_batches(const void* plan);
@@ -779,19 +779,25 @@ int vecchia_plan_neighbors(vecchia_plan_t plan, int32_t* nbr_out) {
 int vecchia_loglik(vecchia_plan_t plan, const double* y_dev, const double theta[4], double* out_dev,
                    void* stream) {
   if (!out_dev) return VECCHIA_EINVAL;
-  return vecchia::launch_loglik(plan, y_dev, theta, false, out_dev, nullptr, (cudaStream_t)stream);
+  return vecchia::launch_loglik(plan, y_dev, theta, false, out_dev, nullptr, (cudaStream_t)stream, 0, -1);
 }
 
 int vecchia_loglik_grad(vecchia_plan_t plan, const double* y_dev, const double theta[4], double* out_dev,
                         void* stream) {
   if (!out_dev) return VECCHIA_EINVAL;
-  return vecchia::launch_loglik(plan, y_dev, theta, true, out_dev, nullptr, (cudaStream_t)stream);
+  return vecchia::launch_loglik(plan, y_dev, theta, true, out_dev, nullptr, (cudaStream_t)stream, 0, -1);
 }
 
 int vecchia_loglik_terms(vecchia_plan_t plan, const double* y_dev, const double theta[4], int want_grad,
                          double* terms_dev, void* stream) {
   if (!terms_dev) return VECCHIA_EINVAL;
-  return vecchia::launch_loglik(plan, y_dev, theta, want_grad != 0, nullptr, terms_dev, (cudaStream_t)stream);
+  return vecchia::launch_loglik(plan, y_dev, theta, want_grad != 0, nullptr, terms_dev, (cudaStream_t)stream, 0, -1);
+}
+
+int vecchia_loglik_range(vecchia_plan_t plan, const double* y_dev, const double theta[4], int64_t i0, int64_t i1,
+                         int want_grad, double* out_dev, void* stream) {
+  if (!out_dev || i0 < 0 || i1 < i0) return VECCHIA_EINVAL;
+  return vecchia::launch_loglik(plan, y_dev, theta, want_grad != 0, out_dev, nullptr, (cudaStream_t)stream, i0, i1);
 }
 
 int vecchia_autotune(vecchia_plan_t plan, const double* y_dev, const double theta[4], int want_grad,
@@ -814,8 +820,12 @@ int vecchia_last_error_location(vecchia_plan_t plan, int64_t* loc) {
   VECCHIA_CUDA_TRY(cudaStreamSynchronize(plan->last_stream));
   unsigned long long v = 0;
   VECCHIA_CUDA_TRY(cudaMemcpy(&v, plan->d_errloc, sizeof(v), cudaMemcpyDeviceToHost));
-  *loc = v == ~0ULL ? -1 : (int64_t)v;
-  return *loc >= 0 ? VECCHIA_ENOTPD : VECCHIA_OK;
+  if (v == ~0ULL) {
+    *loc = -1;
+    return VECCHIA_OK;
+  }
+  *loc = (int64_t)(v >> 2);
+  return (v & 3u) == vecchia::kErrNotPD ? VECCHIA_ENOTPD : VECCHIA_EINVAL;
 }
 
 const char* vecchia_strerror(int code) {

@@ -5,8 +5,9 @@ current CUDA stream.  The library is loaded from this package directory and its
 absence is an error: there is no CPU fallback.
 
 The entry points keep the C names: :func:`vecchia_plan_create` (wrapped by
-:class:`Plan`), :func:`vecchia_loglik`, :func:`vecchia_loglik_grad`,
+:class:`Plan`), :func:`vecchia_loglik`, :func:`vecchia_loglik_grad`, :func:`vecchia_loglik_range`,
 :func:`vecchia_loglik_terms`, :func:`vecchia_matern`, :func:`vecchia_pivot_reciprocal`,
+:func:`vecchia_mul_by_positive`,
 :func:`vecchia_fp64_peak`,
 :func:`vecchia_batched_prepare` and :class:`Batch` (vecchia_loglik_batched),
 :func:`vecchia_loglik_noalloc`;
@@ -22,7 +23,9 @@ import numpy as np
 import torch
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libvecchia.so")
+# VECCHIA_CHECKED=1 selects the bounds-checked build (build.build(checked=True))
+LIB_PATH = os.path.join(HERE, "libvecchia_checked.so" if os.environ.get("VECCHIA_CHECKED", "") == "1"
+                        else "libvecchia.so")
 
 OK, EINVAL, ENOTPD, ECUDA, ETIMEOUT, ENOMEM = range(6)
 ORDER_GIVEN, ORDER_RANDOM, ORDER_MAXMIN, ORDER_MORTON = 0, 1, 2, 3
@@ -54,8 +57,10 @@ SIGNATURES = {
     "vecchia_loglik": (ctypes.c_int, [_vp, _vp, _dp, _vp, _vp]),
     "vecchia_loglik_grad": (ctypes.c_int, [_vp, _vp, _dp, _vp, _vp]),
     "vecchia_loglik_terms": (ctypes.c_int, [_vp, _vp, _dp, ctypes.c_int, _vp, _vp]),
+    "vecchia_loglik_range": (ctypes.c_int, [_vp, _vp, _dp, _i64, _i64, ctypes.c_int, _vp, _vp]),
     "vecchia_matern": (ctypes.c_int, [_vp, _i64, _dp, _vp, _vp, _vp]),
     "vecchia_pivot_reciprocal": (ctypes.c_int, [_vp, _i64, _vp, _vp]),
+    "vecchia_mul_by_positive": (ctypes.c_int, [_vp, _vp, _i64, _vp, _vp]),
     "vecchia_last_error_location": (ctypes.c_int, [_vp, ctypes.POINTER(_i64)]),
     "vecchia_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "vecchia_fp64_peak": (ctypes.c_int, [_dp, _vp]),
@@ -182,6 +187,13 @@ class Plan:
         lib().vecchia_last_error_location(self._h, ctypes.byref(loc))
         return int(loc.value)
 
+    def last_error(self):
+        """(first failing ordered location or -1, status): ENOTPD for a block that is not
+        positive definite, EINVAL for non-finite data, OK for none."""
+        loc = _i64(-1)
+        rc = lib().vecchia_last_error_location(self._h, ctypes.byref(loc))
+        return int(loc.value), int(rc)
+
 
 def vecchia_loglik(plan: Plan, y: torch.Tensor, theta, out: torch.Tensor | None = None, stream=None):
     y = _dev_f64(y, plan.n, "y")
@@ -200,6 +212,18 @@ def vecchia_loglik_grad(plan: Plan, y: torch.Tensor, theta, out: torch.Tensor | 
     rc = lib().vecchia_loglik_grad(plan.handle, _vp(y.data_ptr()), _theta(theta), _vp(out.data_ptr()),
                                    _vp(_stream(stream)))
     _check(rc, "vecchia_loglik_grad")
+    return out
+
+
+def vecchia_loglik_range(plan: Plan, y: torch.Tensor, theta, i0: int, i1: int, want_grad: bool = False,
+                         out: torch.Tensor | None = None, stream=None):
+    """The contribution of ordered locations [i0, i1) to l (and its gradient if want_grad)."""
+    y = _dev_f64(y, plan.n, "y")
+    if out is None:
+        out = torch.empty(4 if want_grad else 1, dtype=torch.float64, device=y.device)
+    rc = lib().vecchia_loglik_range(plan.handle, _vp(y.data_ptr()), _theta(theta), int(i0), int(i1),
+                                    1 if want_grad else 0, _vp(out.data_ptr()), _vp(_stream(stream)))
+    _check(rc, "vecchia_loglik_range")
     return out
 
 
@@ -231,6 +255,17 @@ def vecchia_pivot_reciprocal(d: torch.Tensor, stream=None) -> torch.Tensor:
     out = torch.empty_like(d)
     rc = lib().vecchia_pivot_reciprocal(_vp(d.data_ptr()), d.numel(), _vp(out.data_ptr()), _vp(_stream(stream)))
     _check(rc, "vecchia_pivot_reciprocal")
+    return out
+
+
+def vecchia_mul_by_positive(a: torch.Tensor, b: torch.Tensor, stream=None) -> torch.Tensor:
+    """The kernels' integer column-scaling product a * b (b a positive normal double)."""
+    a = _dev_f64(a, a.numel(), "a")
+    b = _dev_f64(b, a.numel(), "b")
+    out = torch.empty_like(a)
+    rc = lib().vecchia_mul_by_positive(_vp(a.data_ptr()), _vp(b.data_ptr()), a.numel(), _vp(out.data_ptr()),
+                                       _vp(_stream(stream)))
+    _check(rc, "vecchia_mul_by_positive")
     return out
 
 
