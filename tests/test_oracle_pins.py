@@ -309,6 +309,20 @@ def test_kl_ordering_eq5(oracle_mod):
     assert _rel(prev, l0) < 1e-10
 
 
+def test_block_logdensity_matches_scipy(oracle_mod):
+    # log N(y; 0, S) of one dense block against scipy's multivariate normal: a wrong
+    # log-determinant factor, a transposed solve or a dropped 2 pi term would fail here.
+    rng = np.random.default_rng(12)
+    for k in (1, 2, 5, 17, 40):
+        A = rng.standard_normal((k, k))
+        S = A @ A.T + 0.3 * k * np.eye(k)
+        y = 2.0 * rng.standard_normal(k)
+        want = multivariate_normal(mean=np.zeros(k), cov=S).logpdf(y)
+        assert _rel(oracle_mod.block_logdensity(S, y), want) < 1e-12, k
+    with pytest.raises(oracle_mod.OracleNotPD):
+        oracle_mod.block_logdensity(np.array([[1.0, 2.0], [2.0, 1.0]]), np.ones(2))
+
+
 def test_identity_padding_leaves_block_density(oracle_mod):
     # Sec. V-B pads short sets with dummy vectors; identity rows with y = 0 add log N(0;0,1) each.
     rng = np.random.default_rng(0)
