@@ -323,7 +323,8 @@ int vecchia_loglik_noalloc(const double* xy_dev, const double* y_dev, const int3
 /*
  * vecchia_autotune — picks the launch shape of the likelihood kernels for this plan's
  * block size (m + 1) by timing: lanes per location (4, 8, 16 or 32; 32/lanes locations
- * share a warp; 4 lanes take blocks of up to 16 rows, 8 lanes up to 32) and warps per CTA.  Each candidate is timed on the caller's own problem (two
+ * share a warp; 4 lanes take blocks of up to 16 rows, 8 lanes up to 32) and warps per CTA.
+ * Each candidate is timed on the caller's own problem (two
  * timed launches after one warm-up; the fastest wins) and recorded, process-wide, for
  * every later call with the same block size and kind (want_grad) on this device,
  * including the batched call's layouts created afterwards.  Without tuning, blocks of

@@ -334,8 +334,40 @@ __device__ __forceinline__ void beta_pair_add(float2 wr, float2 wc, float2 gr, f
   pbl = __fsub_rn(e, __fsub_rn(pbh, s));
 }
 
+// The adjoint's beta pair sums of one location: this lane's share of
+// sum_{p>q} h(u_pq) (w^_p g_q + w^_q g_p), with h recomputed from the block's float-pair
+// coordinates (pads carry zero weights), two pairs per iteration.  Lane `sub` of the G
+// lanes takes pairs q = sub + G k; w^ and g are float pairs (WHf, GVf).
+template <int G, bool SPHERE>
+__device__ __forceinline__ double beta_pass(const FieldView& F, int NP, const uint32_t* __restrict__ pairs,
+                                            const float2* __restrict__ CX, const float2* __restrict__ CY,
+                                            const float2* __restrict__ CZ, const float2* __restrict__ WHf,
+                                            const float2* __restrict__ GVf, const double* __restrict__ tab,
+                                            const MaternConst& mc, int sub) {
+  float pbh = 0.0f, pbl = 0.0f;
+  for (int q0 = sub; q0 < NP; q0 += 2 * G) {
+    const int q1 = q0 + G;
+    const bool has1 = q1 < NP;
+    const uint32_t w0 = pairs[q0];
+    const uint32_t w1 = has1 ? pairs[q1] : w0;
+    const int r0 = w0 & 0xFF, c0 = (w0 >> 8) & 0xFF;
+    const int r1 = w1 & 0xFF, c1 = (w1 >> 8) & 0xFF;
+    float u0h, u0l, u1h, u1l;
+    pair_u<SPHERE>(F, CX, CY, CZ, r0, c0, u0h, u0l);
+    pair_u<SPHERE>(F, CX, CY, CZ, r1, c1, u1h, u1l);
+    float h0h, h0l, h1h, h1l;
+    h_df(u0h, u0l, tab, mc, h0h, h0l);
+    h_df(u1h, u1l, tab, mc, h1h, h1l);
+    beta_pair_add(WHf[r0], WHf[c0], GVf[r0], GVf[c0], h0h, h0l, pbh, pbl);
+    if (has1) beta_pair_add(WHf[r1], WHf[c1], GVf[r1], GVf[c1], h1h, h1l, pbh, pbl);
+  }
+  return f2d_scaled(pbh, 0) + f2d_scaled(pbl, 0);
+}
+
+// Returns whether the location's term is valid (positive definite block, finite data,
+// indices in range).
 template <bool GRAD, int G, bool SPHERE>
-__device__ __forceinline__ void process_location(int64_t i, bool active, const FieldView& F, const SchedSize& S,
+__device__ __forceinline__ bool process_location(int64_t i, bool active, const FieldView& F, const SchedSize& S,
                                                  const uint16_t* __restrict__ sched,
                                                  const uint32_t* __restrict__ pairs, const WarpArea& W,
                                                  const double* __restrict__ tab, const MaternConst& mc,
@@ -609,7 +641,7 @@ __device__ __forceinline__ void process_location(int64_t i, bool active, const F
   if (!GRAD) {
     if (terms && active && sub == 0) terms[0] = li;
     __syncwarp();
-    return;
+    return good;
   }
   // ---- adjoint: w = L_J^{-T} (row m of L), alpha~ = L_J^{-T} (row K of L)
   double* __restrict__ WH = W.WH;
@@ -681,26 +713,7 @@ __device__ __forceinline__ void process_location(int64_t i, bool active, const F
   }
   const double sS = 0.5 * (rr * rs - 1.0);
   __syncwarp();
-  // beta pair sums: h(u_pq) recomputed from the float-pair coordinates (pads carry
-  // zero weights), two pairs per iteration.
-  float pbh = 0.0f, pbl = 0.0f;
-  for (int q0 = sub; q0 < S.NP; q0 += 2 * G) {
-    const int q1 = q0 + G;
-    const bool has1 = q1 < S.NP;
-    const uint32_t w0 = pairs[q0];
-    const uint32_t w1 = has1 ? pairs[q1] : w0;
-    const int r0 = w0 & 0xFF, c0 = (w0 >> 8) & 0xFF;
-    const int r1 = w1 & 0xFF, c1 = (w1 >> 8) & 0xFF;
-    float u0h, u0l, u1h, u1l;
-    pair_u<SPHERE>(F, CX, CY, CZ, r0, c0, u0h, u0l);
-    pair_u<SPHERE>(F, CX, CY, CZ, r1, c1, u1h, u1l);
-    float h0h, h0l, h1h, h1l;
-    h_df(u0h, u0l, tab, mc, h0h, h0l);
-    h_df(u1h, u1l, tab, mc, h1h, h1l);
-    beta_pair_add(WHf[r0], WHf[c0], GVf[r0], GVf[c0], h0h, h0l, pbh, pbl);
-    if (has1) beta_pair_add(WHf[r1], WHf[c1], GVf[r1], GVf[c1], h1h, h1l, pbh, pbl);
-  }
-  const double pB = f2d_scaled(pbh, 0) + f2d_scaled(pbl, 0);
+  const double pB = beta_pass<G, SPHERE>(F, S.NP, pairs, CX, CY, CZ, WHf, GVf, tab, mc, sub);
   if (terms_mode) {
     const double tB = group_sum<G>(pB), tT = group_sum<G>(pT);
     if (terms && active && sub == 0) {
@@ -722,6 +735,7 @@ __device__ __forceinline__ void process_location(int64_t i, bool active, const F
     }
   }
   __syncwarp();
+  return good;
 }
 
 // Combines the warp's sums into the four output slots
