@@ -156,18 +156,30 @@ __global__ void __launch_bounds__(384) vecchia_batched_kernel(const BatchArgs a)
   }
 }
 
-// One thread per (field, theta): records of the field's tiles in item order.
+// One warp per (field, theta): the field's tile records, each lane a strided subset in
+// item order (compensated), merged by a fixed shuffle tree, so the result depends only
+// on the field's tile count.
 __global__ void vecchia_batched_finalize(const FieldDesc* __restrict__ fields, int nfields, int ntheta,
                                          const double* __restrict__ thetas, const double* __restrict__ partial,
                                          int want_grad, double* out) {
-  const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (id >= (int64_t)nfields * ntheta) return;
+  const int64_t id = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (id >= (int64_t)nfields * ntheta) return;  // whole warps leave together
   const int fs = (int)(id / ntheta), t = (int)(id % ntheta);
   const FieldDesc fd = fields[fs];
   Neumaier acc[4];
   const double* p = partial + (fd.item_base + (int64_t)t * fd.tiles) * 4;
-  for (int k = 0; k < fd.tiles; ++k)
+  for (int k = lane; k < fd.tiles; k += 32)
     for (int c = 0; c < 4; ++c) acc[c].add(p[k * 4 + c]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const double s2 = __shfl_down_sync(0xffffffffu, acc[c].s, o);
+      const double c2 = __shfl_down_sync(0xffffffffu, acc[c].c, o);
+      acc[c].merge(s2, c2);
+    }
+  if (lane != 0) return;
   const int64_t o = (int64_t)fd.orig * ntheta + t;
   if (!want_grad) {
     out[o] = acc[0].value();
@@ -445,7 +457,7 @@ extern "C" int vecchia_loglik_batched(const vecchia_plan_t* plans, const double*
   else vecchia_batched_kernel<false><<<b->blocks, b->W * 32, b->smem, s>>>(a);
   VECCHIA_CUDA_TRY(cudaGetLastError());
   const int64_t pairs = (int64_t)nfields * ntheta;
-  vecchia_batched_finalize<<<(unsigned)((pairs + 127) / 128), 128, 0, s>>>(b->d_fields, nfields, ntheta, thetas_dev,
+  vecchia_batched_finalize<<<(unsigned)((pairs + 3) / 4), 128, 0, s>>>(b->d_fields, nfields, ntheta, thetas_dev,
                                                                            b->d_partial, want_grad, out_dev);
   VECCHIA_CUDA_TRY(cudaGetLastError());
   return VECCHIA_OK;
