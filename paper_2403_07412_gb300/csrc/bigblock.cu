@@ -267,59 +267,60 @@ __global__ void __launch_bounds__(kCtaThreadsMax) vecchia_big_kernel(const BigAr
       __syncthreads();
       continue;
     }
-    // ---- adjoint: backward solves on warp 0, then the pair pass on all threads
+    // ---- adjoint: the two backward solves on warps 0 (w) and 1 (alpha~) at once, then
+    // the pair pass on all threads
     const double rs = rr * inv_s;
     const double cb = 0.5 * (rs * rs - inv_s);
     const double rsa = rs * tc.inv_sigma2;
     double pT = 0.0;
-    if (wid == 0 && good) {
-      // double-float solves on the FP32 pipe, as in the warp kernels: each step of the
-      // serial chain would otherwise wait behind the other CTA's FP64 work
-      constexpr int NS = (kMaxM + 31) / 32;
-      float2 wf[NS], bf[NS];
+    constexpr int NS = (kMaxM + 31) / 32;
+    float2 vf[NS];
+    if (wid < 2 && good) {
+      // Double-float solves on the FP32 pipe, as in the warp kernels: each step of the
+      // serial chain would otherwise wait behind the other CTA's FP64 work.  Warp 0
+      // solves with row m of the factor (w), warp 1 with row K (alpha~); a slot whose
+      // rows are all finished (32 t >= c) is skipped by a warp-uniform test.  Each warp
+      // runs the same operations on its vector as the single warp that used to run both.
+      const int row = wid == 0 ? m : K;
 #pragma unroll
       for (int t = 0; t < NS; ++t) {
         const int c = lane + 32 * t;
-        wf[t] = make_float2(0.0f, 0.0f);
-        bf[t] = make_float2(0.0f, 0.0f);
-        if (c < K - 1) {
-          const int o = tri_off(K, c);
-          wf[t] = d2f_trunc(A[o + m - c]);
-          bf[t] = d2f_trunc(A[o + K - c]);
-        }
+        vf[t] = make_float2(0.0f, 0.0f);
+        if (c < K - 1) vf[t] = d2f_trunc(A[tri_off(K, c) + row - c]);
       }
       for (int c = K - 2; c >= 1; --c) {
         const int src = c & 31, sl = c >> 5;
-        float2 wsel = wf[0], bsel = bf[0];
+        float2 vsel = vf[0];
 #pragma unroll
         for (int t = 1; t < NS; ++t)
-          if (sl == t) {
-            wsel = wf[t];
-            bsel = bf[t];
-          }
-        const float2 wc = make_float2(__shfl_sync(0xffffffffu, wsel.x, src), __shfl_sync(0xffffffffu, wsel.y, src));
-        const float2 bc = make_float2(__shfl_sync(0xffffffffu, bsel.x, src), __shfl_sync(0xffffffffu, bsel.y, src));
+          if (sl == t) vsel = vf[t];
+        const float2 vc = make_float2(__shfl_sync(0xffffffffu, vsel.x, src), __shfl_sync(0xffffffffu, vsel.y, src));
 #pragma unroll
         for (int t = 0; t < NS; ++t) {
+          if (32 * t >= c) break;  // uniform over the warp
           const int cc = lane + 32 * t;
           if (cc < c) {
             const float2 l = d2f_trunc(A[tri_off(K, cc) + c - cc]);
-            df_fms(wf[t].x, wf[t].y, l, wc);
-            df_fms(bf[t].x, bf[t].y, l, bc);
+            df_fms(vf[t].x, vf[t].y, l, vc);
           }
         }
       }
-      double w[NS], bv[NS];
+      if (wid == 1) {  // alpha~ to warp 0 through YV (free after the elimination), exactly
 #pragma unroll
-      for (int t = 0; t < NS; ++t) {
-        w[t] = f2d_scaled(wf[t].x, 0) + f2d_scaled(wf[t].y, 0);
-        bv[t] = f2d_scaled(bf[t].x, 0) + f2d_scaled(bf[t].y, 0);
+        for (int t = 0; t < NS; ++t) {
+          const int c = lane + 32 * t;
+          if (c < K - 1) YV[c] = f2d_scaled(vf[t].x, 0) + f2d_scaled(vf[t].y, 0);
+        }
       }
+    }
+    __syncthreads();
+    if (wid == 0 && good) {
 #pragma unroll
       for (int t = 0; t < NS; ++t) {
         const int c = lane + 32 * t;
         if (c < K - 1) {
-          const double wh = -w[t], gv = fma(rsa, bv[t], cb * wh);
+          const double w = f2d_scaled(vf[t].x, 0) + f2d_scaled(vf[t].y, 0);
+          const double wh = -w, gv = fma(rsa, YV[c], cb * wh);
           WHf[c] = d2f_pair(wh);
           GVf[c] = d2f_pair(gv);
           pT = fma(wh, gv, pT);
@@ -334,13 +335,21 @@ __global__ void __launch_bounds__(kCtaThreadsMax) vecchia_big_kernel(const BigAr
     __syncthreads();
     float pbh = 0.0f, pbl = 0.0f;
     if (good) {
-      for (int q0 = tid; q0 < NP; q0 += NTH) {
-        const int v0 = tri_root(q0);
+      // two pairs per iteration (q0, q0 + NTH), added in the same order as one at a time
+      for (int q0 = tid; q0 < NP; q0 += 2 * NTH) {
+        const int q1 = q0 + NTH;
+        const bool has1 = q1 < NP;
+        const int v0 = tri_root(q0), v1 = tri_root(has1 ? q1 : q0);
         const int c0 = K - 2 - v0, r0 = c0 + 1 + (q0 - v0 * (v0 + 1) / 2);
-        float uh, ul, hh, hl;
-        pair_u<SPHERE>(F, CX, CY, CZ, r0, c0, uh, ul);
-        h_df(uh, ul, a.tab, mc, hh, hl);
-        beta_pair_add(WHf[r0], WHf[c0], GVf[r0], GVf[c0], hh, hl, pbh, pbl);
+        const int qq1 = has1 ? q1 : q0;
+        const int c1 = K - 2 - v1, r1 = c1 + 1 + (qq1 - v1 * (v1 + 1) / 2);
+        float u0h, u0l, u1h, u1l, h0h, h0l, h1h, h1l;
+        pair_u<SPHERE>(F, CX, CY, CZ, r0, c0, u0h, u0l);
+        pair_u<SPHERE>(F, CX, CY, CZ, r1, c1, u1h, u1l);
+        h_df(u0h, u0l, a.tab, mc, h0h, h0l);
+        h_df(u1h, u1l, a.tab, mc, h1h, h1l);
+        beta_pair_add(WHf[r0], WHf[c0], GVf[r0], GVf[c0], h0h, h0l, pbh, pbl);
+        if (has1) beta_pair_add(WHf[r1], WHf[c1], GVf[r1], GVf[c1], h1h, h1l, pbh, pbl);
       }
     }
     const double pB = f2d_scaled(pbh, 0) + f2d_scaled(pbl, 0);
