@@ -465,6 +465,13 @@ __device__ __forceinline__ bool process_location(int64_t i, bool active, const F
   // single-column steps, with half the column transitions and shared-memory passes).
   bool ok = true;
   double* __restrict__ TV1 = YV;  // column j+1's unscaled entries (YV is free after assembly)
+  // Column scaling by the pivot reciprocal: the integer round-to-nearest-even product
+  // (mul_by_positive, bit-identical to the DMUL) in the full-warp forward kernel, where
+  // it keeps an FP64 instruction off the column step's serial path (n = 1M, m = 60:
+  // 89.5 -> 86.4 ms); the DMUL in the gradient kernel, whose double-float adjoint leaves
+  // the FP64 queue shorter (103.4 -> 100.0 ms with the DMUL), and in narrow groups, where
+  // one DMUL serves 32/G locations.
+  constexpr bool kIntScale = G == 32 && !GRAD;
   int j = 0;
   for (; j + 2 < K; j += 2) {
     const int oj = tri_off(K, j), o1 = tri_off(K, j + 1);
@@ -474,7 +481,7 @@ __device__ __forceinline__ bool process_location(int64_t i, bool active, const F
     for (int r = j + 1 + sub; r <= K; r += G) {
       const double tv = A[oj + r - j];
       TV[r] = tv;
-      if constexpr (G == 32) {
+      if constexpr (kIntScale) {
         A[oj + r - j] = mul_by_positive(tv, inv0);
       } else {
         A[oj + r - j] = tv * inv0;
@@ -496,7 +503,7 @@ __device__ __forceinline__ bool process_location(int64_t i, bool active, const F
     for (int r = j + 2 + sub; r <= K; r += G) {
       const double tv = A[o1 + r - j - 1];
       TV1[r] = tv;
-      if constexpr (G == 32) {
+      if constexpr (kIntScale) {
         A[o1 + r - j - 1] = mul_by_positive(tv, inv1);
       } else {
         A[o1 + r - j - 1] = tv * inv1;
@@ -585,9 +592,9 @@ __device__ __forceinline__ bool process_location(int64_t i, bool active, const F
     for (int r = j + 1 + sub; r <= K; r += G) {
       const double tv = A[oj + r - j];
       TV[r] = tv;
-      // full-warp groups: integer product (no wait behind other warps' FP64 work on the
-      // column step's serial path); narrow groups amortise one DMUL over 32/G locations
-      if constexpr (G == 32) {
+      // integer product in the full-warp forward kernel (no wait behind other warps'
+      // FP64 work on the column step's serial path); DMUL elsewhere (kIntScale)
+      if constexpr (kIntScale) {
         A[oj + r - j] = mul_by_positive(tv, inv);
       } else {
         A[oj + r - j] = tv * inv;
