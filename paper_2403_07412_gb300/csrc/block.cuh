@@ -337,10 +337,9 @@ __device__ __forceinline__ void beta_pair_add(float2 wr, float2 wc, float2 gr, f
 // The adjoint's beta pair sums of one location: this lane's share of
 // sum_{p>q} h(u_pq) (w^_p g_q + w^_q g_p), with h recomputed from the block's float-pair
 // coordinates (pads carry zero weights).  Lane `sub` of the G lanes takes pairs
-// q = sub + G k, in increasing k; w^ and g are float pairs (WHf, GVf).  Full-warp groups
-// take one pair per iteration (fewer live registers: n = 1M, m = 60, l + grad 101.2 ->
-// 99.3 ms against two pairs), narrow groups two, so one pair's loads overlap the other's
-// arithmetic; the sums are the same either way.
+// q = sub + G k, in increasing k; w^ and g are float pairs (WHf, GVf).  One pair per
+// iteration: fewer live registers than two (n = 1M, m = 60, l + grad 101.2 -> 99.3 ms;
+// at n = 250k, m = 20, 2.03 -> 1.98 ms), with the same sums.
 template <int G, bool SPHERE>
 __device__ __forceinline__ double beta_pass(const FieldView& F, int NP, const uint32_t* __restrict__ pairs,
                                             const float2* __restrict__ CX, const float2* __restrict__ CY,
@@ -348,32 +347,13 @@ __device__ __forceinline__ double beta_pass(const FieldView& F, int NP, const ui
                                             const float2* __restrict__ GVf, const double* __restrict__ tab,
                                             const MaternConst& mc, int sub) {
   float pbh = 0.0f, pbl = 0.0f;
-  if constexpr (G == 32) {
-    for (int q0 = sub; q0 < NP; q0 += G) {
-      const uint32_t w0 = pairs[q0];
-      const int r0 = w0 & 0xFF, c0 = (w0 >> 8) & 0xFF;
-      float u0h, u0l, h0h, h0l;
-      pair_u<SPHERE>(F, CX, CY, CZ, r0, c0, u0h, u0l);
-      h_df(u0h, u0l, tab, mc, h0h, h0l);
-      beta_pair_add(WHf[r0], WHf[c0], GVf[r0], GVf[c0], h0h, h0l, pbh, pbl);
-    }
-    return f2d_scaled(pbh, 0) + f2d_scaled(pbl, 0);
-  }
-  for (int q0 = sub; q0 < NP; q0 += 2 * G) {
-    const int q1 = q0 + G;
-    const bool has1 = q1 < NP;
+  for (int q0 = sub; q0 < NP; q0 += G) {
     const uint32_t w0 = pairs[q0];
-    const uint32_t w1 = has1 ? pairs[q1] : w0;
     const int r0 = w0 & 0xFF, c0 = (w0 >> 8) & 0xFF;
-    const int r1 = w1 & 0xFF, c1 = (w1 >> 8) & 0xFF;
-    float u0h, u0l, u1h, u1l;
+    float u0h, u0l, h0h, h0l;
     pair_u<SPHERE>(F, CX, CY, CZ, r0, c0, u0h, u0l);
-    pair_u<SPHERE>(F, CX, CY, CZ, r1, c1, u1h, u1l);
-    float h0h, h0l, h1h, h1l;
     h_df(u0h, u0l, tab, mc, h0h, h0l);
-    h_df(u1h, u1l, tab, mc, h1h, h1l);
     beta_pair_add(WHf[r0], WHf[c0], GVf[r0], GVf[c0], h0h, h0l, pbh, pbl);
-    if (has1) beta_pair_add(WHf[r1], WHf[c1], GVf[r1], GVf[c1], h1h, h1l, pbh, pbl);
   }
   return f2d_scaled(pbh, 0) + f2d_scaled(pbl, 0);
 }
