@@ -6,8 +6,9 @@
 // bordered L D L^T whose trailing 2x2 corner holds s_i / sigma2 and y_i - mu_i) with
 // CTA-wide barriers.  The (row, column) of a packed slot or a pair index is decoded
 // arithmetically (a triangular-number inverse) instead of from schedule tables, which
-// keeps two CTAs resident per SM.  The adjoint's two backward solves run on the first
-// warp (shuffles); everything else is spread over all threads.
+// keeps two CTAs resident per SM.  The adjoint's two backward solves run on the first two
+// warps, one each, on vectors in shared memory; everything else is spread over all
+// threads.
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
@@ -273,58 +274,39 @@ __global__ void __launch_bounds__(kCtaThreadsMax) vecchia_big_kernel(const BigAr
     const double cb = 0.5 * (rs * rs - inv_s);
     const double rsa = rs * tc.inv_sigma2;
     double pT = 0.0;
-    constexpr int NS = (kMaxM + 31) / 32;
-    float2 vf[NS];
     if (wid < 2 && good) {
       // Double-float solves on the FP32 pipe, as in the warp kernels: each step of the
-      // serial chain would otherwise wait behind the other CTA's FP64 work.  Warp 0
-      // solves with row m of the factor (w), warp 1 with row K (alpha~); a slot whose
-      // rows are all finished (32 t >= c) is skipped by a warp-uniform test.  Each warp
-      // runs the same operations on its vector as the single warp that used to run both.
+      // serial chain would otherwise wait behind the other CTAs' FP64 work.  Warp 0
+      // solves with row m of the factor (w) in TV, warp 1 with row K (alpha~) in YV (both
+      // free after the elimination).  The vectors live in shared memory, not registers:
+      // held in registers they took the kernel from 80 to 122 registers per thread and
+      // one CTA per SM of occupancy at m = 90 and 120.
+      float2* V = reinterpret_cast<float2*>(wid == 0 ? TV : YV);
       const int row = wid == 0 ? m : K;
-#pragma unroll
-      for (int t = 0; t < NS; ++t) {
-        const int c = lane + 32 * t;
-        vf[t] = make_float2(0.0f, 0.0f);
-        if (c < K - 1) vf[t] = d2f_trunc(A[tri_off(K, c) + row - c]);
-      }
+      for (int c = lane; c < K - 1; c += 32) V[c] = d2f_trunc(A[tri_off(K, c) + row - c]);
+      __syncwarp();
       for (int c = K - 2; c >= 1; --c) {
-        const int src = c & 31, sl = c >> 5;
-        float2 vsel = vf[0];
-#pragma unroll
-        for (int t = 1; t < NS; ++t)
-          if (sl == t) vsel = vf[t];
-        const float2 vc = make_float2(__shfl_sync(0xffffffffu, vsel.x, src), __shfl_sync(0xffffffffu, vsel.y, src));
-#pragma unroll
-        for (int t = 0; t < NS; ++t) {
-          if (32 * t >= c) break;  // uniform over the warp
-          const int cc = lane + 32 * t;
-          if (cc < c) {
-            const float2 l = d2f_trunc(A[tri_off(K, cc) + c - cc]);
-            df_fms(vf[t].x, vf[t].y, l, vc);
-          }
+        const float2 vc = V[c];  // final since the previous step (__syncwarp below)
+        for (int cc = lane; cc < c; cc += 32) {
+          const float2 l = d2f_trunc(A[tri_off(K, cc) + c - cc]);
+          float2 v = V[cc];
+          df_fms(v.x, v.y, l, vc);
+          V[cc] = v;
         }
-      }
-      if (wid == 1) {  // alpha~ to warp 0 through YV (free after the elimination), exactly
-#pragma unroll
-        for (int t = 0; t < NS; ++t) {
-          const int c = lane + 32 * t;
-          if (c < K - 1) YV[c] = f2d_scaled(vf[t].x, 0) + f2d_scaled(vf[t].y, 0);
-        }
+        __syncwarp();
       }
     }
     __syncthreads();
     if (wid == 0 && good) {
-#pragma unroll
-      for (int t = 0; t < NS; ++t) {
-        const int c = lane + 32 * t;
-        if (c < K - 1) {
-          const double w = f2d_scaled(vf[t].x, 0) + f2d_scaled(vf[t].y, 0);
-          const double wh = -w, gv = fma(rsa, YV[c], cb * wh);
-          WHf[c] = d2f_pair(wh);
-          GVf[c] = d2f_pair(gv);
-          pT = fma(wh, gv, pT);
-        }
+      const float2* Vw = reinterpret_cast<const float2*>(TV);
+      const float2* Va = reinterpret_cast<const float2*>(YV);
+      for (int c = lane; c < K - 1; c += 32) {
+        const double w = f2d_scaled(Vw[c].x, 0) + f2d_scaled(Vw[c].y, 0);
+        const double al = f2d_scaled(Va[c].x, 0) + f2d_scaled(Va[c].y, 0);
+        const double wh = -w, gv = fma(rsa, al, cb * wh);
+        WHf[c] = d2f_pair(wh);
+        GVf[c] = d2f_pair(gv);
+        pT = fma(wh, gv, pT);
       }
       if (lane == 0) {
         WHf[m] = make_float2(1.0f, 0.0f);
@@ -334,22 +316,14 @@ __global__ void __launch_bounds__(kCtaThreadsMax) vecchia_big_kernel(const BigAr
     }
     __syncthreads();
     float pbh = 0.0f, pbl = 0.0f;
-    if (good) {
-      // two pairs per iteration (q0, q0 + NTH), added in the same order as one at a time
-      for (int q0 = tid; q0 < NP; q0 += 2 * NTH) {
-        const int q1 = q0 + NTH;
-        const bool has1 = q1 < NP;
-        const int v0 = tri_root(q0), v1 = tri_root(has1 ? q1 : q0);
+    if (good) {  // one pair per iteration (two took more registers, no less time)
+      for (int q0 = tid; q0 < NP; q0 += NTH) {
+        const int v0 = tri_root(q0);
         const int c0 = K - 2 - v0, r0 = c0 + 1 + (q0 - v0 * (v0 + 1) / 2);
-        const int qq1 = has1 ? q1 : q0;
-        const int c1 = K - 2 - v1, r1 = c1 + 1 + (qq1 - v1 * (v1 + 1) / 2);
-        float u0h, u0l, u1h, u1l, h0h, h0l, h1h, h1l;
+        float u0h, u0l, h0h, h0l;
         pair_u<SPHERE>(F, CX, CY, CZ, r0, c0, u0h, u0l);
-        pair_u<SPHERE>(F, CX, CY, CZ, r1, c1, u1h, u1l);
         h_df(u0h, u0l, a.tab, mc, h0h, h0l);
-        h_df(u1h, u1l, a.tab, mc, h1h, h1l);
         beta_pair_add(WHf[r0], WHf[c0], GVf[r0], GVf[c0], h0h, h0l, pbh, pbl);
-        if (has1) beta_pair_add(WHf[r1], WHf[c1], GVf[r1], GVf[c1], h1h, h1l, pbh, pbl);
       }
     }
     const double pB = f2d_scaled(pbh, 0) + f2d_scaled(pbl, 0);
