@@ -86,7 +86,7 @@ __device__ __forceinline__ void run_item(const FieldDesc& fd, int64_t tile, cons
   const SchedSize S(K);
   const uint16_t* sched = reinterpret_cast<const uint16_t*>(smem + a.sched_off[fd.kidx]);
   const uint32_t* pairs = reinterpret_cast<const uint32_t*>(smem + a.pairs_off[fd.kidx]);
-  const WarpArea area(base + grp * WarpArea::doubles(K, GRAD), K);
+  const WarpArea area(base + grp * WarpArea::doubles(K, GRAD), K, GRAD);
   Accum acc;
   const int64_t i0 = tile * kTile;
   const int64_t i1 = min(fd.n, i0 + kTile);

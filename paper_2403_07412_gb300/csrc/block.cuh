@@ -53,28 +53,44 @@ struct SchedSize {
   }
 };
 
-// Per-warp shared-memory area for blocks up to size K: the packed triangle A, the
-// block rows' coordinates CX, CY (float pairs), the data YV (assembly only) and the
-// pivot column TV (elimination only).  The adjoint's weight vectors WH and GV reuse
-// YV and TV, so the gradient kernel fits as many warps per SM as the forward one.
-// On the sphere a third coordinate array CZ follows CY.
+// Per-warp shared-memory area for blocks up to size K: the packed triangle A and the
+// block rows' coordinates CX, CY (float pairs; on the sphere a third array CZ follows CY).
+// The data go straight into A's border row.  The elimination's two column buffers TV and
+// TV1 hold the unscaled entries of columns j and j+1:
+//  - forward kernel: they reuse CX and CY, which are dead after the assembly, so a block
+//    takes two vectors besides A (at m = 60, 16.6 KB instead of 17.6 KB: thirteen
+//    32-lane blocks fit on an SM instead of twelve);
+//  - gradient kernel: the adjoint's pair pass needs the coordinates again, so TV and TV1
+//    are separate (TV1 holds the data until the assembly), and after the elimination the
+//    weight vectors w^ and g (float pairs) take their places.  Gathering the coordinates
+//    a second time instead cost more than the extra warps gained (n = 1M, m = 60: 99.0 ->
+//    102.3 ms; m = 45: 48.2 -> 50.0 ms).
 struct WarpArea {
-  double *A, *YV, *TV, *WH, *GV;
+  double* A;
   float2 *CX, *CY, *CZ;
-  __host__ __device__ static int doubles(int K, bool /*grad*/, bool sphere = false) {
+  double *TV, *TV1;   // elimination: unscaled entries of columns j and j+1
+  float2 *WHf, *GVf;  // gradient, after the elimination: w^ and g as float pairs
+  __host__ __device__ static int doubles(int K, bool grad, bool sphere = false) {
     const SchedSize S(K);
-    return align_up(S.NT, 2) + (sphere ? 5 : 4) * align_up(K + 1, 2);
+    return align_up(S.NT, 2) + ((sphere ? 3 : 2) + (grad ? 2 : 0)) * align_up(K + 1, 2);
   }
-  __device__ WarpArea(double* base, int K, bool sphere = false) {
+  __device__ WarpArea(double* base, int K, bool grad, bool sphere = false) {
     const SchedSize S(K);
+    const int V = align_up(K + 1, 2);
     A = base;
     CX = reinterpret_cast<float2*>(A + align_up(S.NT, 2));
-    CY = CX + align_up(K + 1, 2);
-    CZ = sphere ? CY + align_up(K + 1, 2) : CY;
-    YV = reinterpret_cast<double*>(CY + (sphere ? 2 : 1) * align_up(K + 1, 2));
-    TV = YV + align_up(K + 1, 2);
-    WH = YV;
-    GV = TV;
+    CY = CX + V;
+    CZ = sphere ? CY + V : CY;
+    if (grad) {
+      TV = reinterpret_cast<double*>(CY + (sphere ? 2 : 1) * V);
+      TV1 = TV + V;
+      WHf = reinterpret_cast<float2*>(TV1);
+      GVf = reinterpret_cast<float2*>(TV);
+    } else {
+      TV = reinterpret_cast<double*>(CX);
+      TV1 = reinterpret_cast<double*>(CY);
+      WHf = GVf = nullptr;
+    }
   }
 };
 
@@ -358,6 +374,22 @@ __device__ __forceinline__ double beta_pass(const FieldView& F, int NP, const ui
   return f2d_scaled(pbh, 0) + f2d_scaled(pbl, 0);
 }
 
+// Offsets of neighbour j from the location js: centred, 1/beta-scaled plane coordinates,
+// or unit-vector differences on the sphere (the length scale enters through K2 there).
+template <bool SPHERE>
+__device__ __forceinline__ void coord_offsets(const FieldView& F, const ThetaConst& tc, double2 ps, int js, int j,
+                                              double& xv, double& yv, double& zv) {
+  if constexpr (SPHERE) {
+    xv = F.xyz[3 * j] - F.xyz[3 * js];
+    yv = F.xyz[3 * j + 1] - F.xyz[3 * js + 1];
+    zv = F.xyz[3 * j + 2] - F.xyz[3 * js + 2];
+  } else {
+    const double2 q = F.xy[j];
+    xv = (q.x - ps.x) * tc.inv_len;
+    yv = (q.y - ps.y) * tc.inv_len;
+  }
+}
+
 // Returns whether the location's term is valid (positive definite block, finite data,
 // indices in range).
 template <bool GRAD, int G, bool SPHERE>
@@ -375,7 +407,6 @@ __device__ __forceinline__ bool process_location(int64_t i, bool active, const F
   float2* __restrict__ CX = W.CX;
   float2* __restrict__ CY = W.CY;
   float2* __restrict__ CZ = W.CZ;
-  double* __restrict__ YV = W.YV;
   double* __restrict__ TV = W.TV;
   const int mi = (i < m && !F.pmean) ? (int)i : m;
   const int32_t* __restrict__ row = F.nbr + i * m;
@@ -387,7 +418,10 @@ __device__ __forceinline__ bool process_location(int64_t i, bool active, const F
     js = 0;
   }
   const double2 ps = F.xy[js];
-  // ---- gather: centred, 1/beta-scaled coordinates (as float pairs) and data
+  // ---- gather: centred, 1/beta-scaled coordinates (as float pairs), and the data: in the
+  // forward kernel straight into the border row K of A (slot tri_off(K, c) + K - c; the
+  // location's own y lands in A[2]), in the gradient kernel into TV1, copied to the border
+  // by the assembly (that order measured 1% faster there)
 #pragma unroll
   for (int s = 0; s < NSG; ++s) {
     const int p = sub + G * s;
@@ -399,18 +433,14 @@ __device__ __forceinline__ bool process_location(int64_t i, bool active, const F
           bad_idx = true;
           j = 0;
         }
-        if constexpr (SPHERE) {  // unit-vector offsets; the length scale enters through K2
-          xv = F.xyz[3 * j] - F.xyz[3 * js];
-          yv = F.xyz[3 * j + 1] - F.xyz[3 * js + 1];
-          zv = F.xyz[3 * j + 2] - F.xyz[3 * js + 2];
-        } else {
-          const double2 q = F.xy[j];
-          xv = (q.x - ps.x) * tc.inv_len;
-          yv = (q.y - ps.y) * tc.inv_len;
-        }
+        coord_offsets<SPHERE>(F, tc, ps, js, j, xv, yv, zv);
         fv = F.yf[j];
       }
-      YV[p] = fv;
+      if constexpr (GRAD) {
+        W.TV1[p] = fv;
+      } else {
+        A[tri_off(K, p) + K - p] = fv;
+      }
       CX[p] = d2f_pair(xv);
       CY[p] = d2f_pair(yv);
       if constexpr (SPHERE) CZ[p] = d2f_pair(zv);
@@ -420,7 +450,11 @@ __device__ __forceinline__ bool process_location(int64_t i, bool active, const F
     CX[m] = make_float2(0.0f, 0.0f);
     CY[m] = make_float2(0.0f, 0.0f);
     if constexpr (SPHERE) CZ[m] = make_float2(0.0f, 0.0f);
-    YV[m] = F.yf[js];
+    if constexpr (GRAD) {
+      W.TV1[m] = F.yf[js];
+    } else {
+      A[tri_off(K, m) + K - m] = F.yf[js];
+    }
   }
   if (check) {  // a bad index anywhere in the group fails the group's block
     const unsigned lane = threadIdx.x & 31u;
@@ -428,11 +462,12 @@ __device__ __forceinline__ bool process_location(int64_t i, bool active, const F
     bad_idx = (__ballot_sync(0xffffffffu, bad_idx) & gmask) != 0u;
   }
   __syncwarp();
-  // ---- assemble: diagonal, data border, then the correlation pairs
+  // ---- assemble: diagonal (and in the gradient kernel the data border), then the
+  // correlation pairs
   for (int c = sub; c < K; c += G) {
     const int o = tri_off(K, c);
     A[o] = (c >= mi && c < m) ? 1.0 : tc.gamma1;
-    A[o + K - c] = YV[c];
+    if constexpr (GRAD) A[o + K - c] = W.TV1[c];
   }
   if (sub == 0) A[0] = 0.0;
   // Two pairs per lane per iteration so one pair's loads overlap the other's FMAs.
@@ -458,7 +493,7 @@ __device__ __forceinline__ bool process_location(int64_t i, bool active, const F
   // both (fma(-L1, T1, fma(-L0, T0, a)): the same roundings, in the same order, as two
   // single-column steps, with half the column transitions and shared-memory passes).
   bool ok = true;
-  double* __restrict__ TV1 = YV;  // column j+1's unscaled entries (YV is free after assembly)
+  double* __restrict__ TV1 = W.TV1;  // column j+1's unscaled entries
   // Column scaling by the pivot reciprocal: the integer round-to-nearest-even product
   // (mul_by_positive, bit-identical to the DMUL) in the full-warp forward kernel, where
   // it keeps an FP64 instruction off the column step's serial path (n = 1M, m = 60:
@@ -674,8 +709,6 @@ __device__ __forceinline__ bool process_location(int64_t i, bool active, const F
     return good;
   }
   // ---- adjoint: w = L_J^{-T} (row m of L), alpha~ = L_J^{-T} (row K of L)
-  double* __restrict__ WH = W.WH;
-  double* __restrict__ GV = W.GV;
   constexpr int NS = (KCAP - 1 + G - 1) / G;  // slots of the K-1 <= KCAP-1 neighbour entries
   // The two unit backward solves run in double-float arithmetic on the FP32 pipe: each
   // step of their serial chain would otherwise wait behind the other warps' FP64 work.
@@ -723,8 +756,8 @@ __device__ __forceinline__ bool process_location(int64_t i, bool active, const F
   const double rsa = rs * tc.inv_sigma2;  // alpha = alpha~ / sigma2
   // w^ and g are kept as float pairs for the beta pair sums below (double-float products
   // there: the same ~2^-46 relative precision as h(u) itself, and no FP64 instruction).
-  float2* __restrict__ WHf = reinterpret_cast<float2*>(WH);
-  float2* __restrict__ GVf = reinterpret_cast<float2*>(GV);
+  float2* __restrict__ WHf = W.WHf;
+  float2* __restrict__ GVf = W.GVf;
   double pT = 0.0;
 #pragma unroll
   for (int t = 0; t < NS; ++t) {

@@ -28,6 +28,9 @@ constexpr size_t kTableBytes = (size_t)16 * kIntWords * kNInt + sizeof(double) *
 // Largest conditioning sets: overall (CTA-per-location kernel) and for the warp kernels.
 constexpr int kMaxM = VECCHIA_MAX_M;
 constexpr int kMaxMWarp = VECCHIA_MAX_M_WARP;
+// Most warps in one CTA of the warp kernels: thirteen 32-lane blocks of m = 60 fill the
+// 227 KB of shared memory a CTA may hold.
+constexpr int kMaxCtaWarps = 13;
 // Largest block (K = m + 1 rows) a group of G lanes per location handles: narrow groups
 // keep at most four neighbour slots per lane, so their per-lane register arrays (and the
 // selects that index them) stay short.

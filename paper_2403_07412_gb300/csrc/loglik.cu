@@ -98,7 +98,7 @@ struct SmemLayout {
 };
 
 template <bool GRAD, int G, bool SPHERE>
-__global__ void __launch_bounds__(384) vecchia_lik_kernel(const LikArgs a) {
+__global__ void __launch_bounds__(GRAD ? 384 : 32 * kMaxCtaWarps) vecchia_lik_kernel(const LikArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int NL = 32 / G;
   const int K = a.m + 1;
@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(384) vecchia_lik_kernel(const LikArgs a) {
   const int W = blockDim.x >> 5;
   const int grp = lane / G, sub = lane % G;
   const WarpArea area(reinterpret_cast<double*>(smem + L.S.sched_bytes + L.S.pairs_bytes) +
-                          wib * L.per_warp_doubles + grp * L.group_doubles, K, sphere);
+                          wib * L.per_warp_doubles + grp * L.group_doubles, K, GRAD, sphere);
   build_schedules(K, sched, pairs);
   __syncthreads();
 
@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(384) vecchia_lik_kernel(const LikArgs a) {
                               a.errloc, sub);
   }
   // The CTA's warps' sums are combined in warp order (compensated), one record per CTA.
-  __shared__ double wpart[12][4];
+  __shared__ double wpart[kMaxCtaWarps][4];
   write_partial<G>(acc, wpart[wib], lane);
   __syncthreads();
   if (threadIdx.x < 4) {
@@ -259,9 +259,12 @@ int shape_for(int K, bool grad, int G, int forced_W, LaunchCfg* cfg, bool sphere
   VECCHIA_CUDA_TRY(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   const SmemLayout L(K, grad, G, sphere);
   void* kern = lik_kernel(grad, G, sphere);
+  cudaFuncAttributes fa;
+  VECCHIA_CUDA_TRY(cudaFuncGetAttributes(&fa, kern));  // the forward kernel takes up to 13 warps
   int best_warps = -1;
-  for (int W : {12, 11, 10, 9, 8, 6, 4, 2, 1}) {
+  for (int W : {13, 12, 11, 10, 9, 8, 6, 4, 2, 1}) {
     if (forced_W > 0 && W != forced_W) continue;
+    if (32 * W > fa.maxThreadsPerBlock) continue;
     const int bytes = L.bytes(W);
     if (bytes > smem_optin) continue;
     VECCHIA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
@@ -572,7 +575,7 @@ int autotune(Plan* p, const double* y_dev, const double* theta, bool grad, int* 
   int bestG = default_lanes(K, grad), bestW = 0, rc = VECCHIA_OK;
   for (int G : {4, 8, 16, 32}) {
     if (K > max_k_for_lanes(G)) continue;
-    for (int W : {12, 11, 10, 9, 8, 6, 4}) {
+    for (int W : {13, 12, 11, 10, 9, 8, 6, 4}) {
       LaunchCfg cfg;
       if (shape_for(K, grad, G, W, &cfg, p->metric == 1) != VECCHIA_OK) continue;
       float tmin = 1e30f;
