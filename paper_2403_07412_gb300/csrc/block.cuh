@@ -497,10 +497,11 @@ __device__ __forceinline__ bool process_location(int64_t i, bool active, const F
   // Column scaling by the pivot reciprocal: the integer round-to-nearest-even product
   // (mul_by_positive, bit-identical to the DMUL) in the full-warp forward kernel, where
   // it keeps an FP64 instruction off the column step's serial path (n = 1M, m = 60:
-  // 89.5 -> 86.4 ms); the DMUL in the gradient kernel, whose double-float adjoint leaves
-  // the FP64 queue shorter (103.4 -> 100.0 ms with the DMUL), and in narrow groups, where
-  // one DMUL serves 32/G locations.
-  constexpr bool kIntScale = G == 32 && !GRAD;
+  // 89.5 -> 86.4 ms), and in the 4-lane forward kernel (m = 10: 1.266 -> 1.245 ms); the
+  // DMUL in the gradient kernel, whose double-float adjoint leaves the FP64 queue shorter
+  // (103.4 -> 100.0 ms with the DMUL), and in 8- and 16-lane groups (2.5% faster at
+  // m = 30).
+  constexpr bool kIntScale = (G == 32 || G == 4) && !GRAD;
   int j = 0;
   for (; j + 2 < K; j += 2) {
     const int oj = tri_off(K, j), o1 = tri_off(K, j + 1);
