@@ -45,7 +45,7 @@ enum {
   VECCHIA_EINVAL = 1,   /* an argument is out of range or not finite            */
   VECCHIA_ENOTPD = 2,   /* a conditional block was not positive definite        */
   VECCHIA_ECUDA = 3,    /* a CUDA runtime call failed                           */
-  VECCHIA_ETIMEOUT = 4, /* a bounded device-side wait expired                   */
+  VECCHIA_ETIMEOUT = 4, /* reserved: no kernel of this library waits on another */
   VECCHIA_ENOMEM = 5    /* device or host allocation failed                     */
 };
 
