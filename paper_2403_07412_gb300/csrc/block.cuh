@@ -53,35 +53,52 @@ struct SchedSize {
   }
 };
 
+// Whether the gradient kernel with G lanes per location may gather the block's
+// coordinates a second time after the elimination, so that its block fits the forward
+// kernel's two vectors (the launch decides, see shape_for in loglik.cu).  With 8 lanes
+// (m = 16..31) shared memory can limit the warps per SM: at n = 1M, fwd + grad at m = 25
+// went from 13.48 to 12.54 ms (12 -> 16 warps per SM) and at m = 30 from 21.80 to 21.07
+// ms (10 -> 12), but at m = 31 (10 -> 11 warps) from 22.24 to 22.33 ms and at m = 20
+// (16 warps either way) from 7.69 to 8.05 ms.  With 32 lanes the second gather costs more
+// than the thirteenth warp gains (m = 60: 99.0 -> 102.3 ms; m = 45: 48.2 -> 50.0 ms), and
+// with 4 lanes the registers, not shared memory, limit the warps.
+__host__ __device__ constexpr bool regather_capable(bool grad, int G) { return grad && G == 8; }
+
 // Per-warp shared-memory area for blocks up to size K: the packed triangle A and the
 // block rows' coordinates CX, CY (float pairs; on the sphere a third array CZ follows CY).
-// The data go straight into A's border row.  The elimination's two column buffers TV and
-// TV1 hold the unscaled entries of columns j and j+1:
-//  - forward kernel: they reuse CX and CY, which are dead after the assembly, so a block
-//    takes two vectors besides A (at m = 60, 16.6 KB instead of 17.6 KB: thirteen
-//    32-lane blocks fit on an SM instead of twelve);
-//  - gradient kernel: the adjoint's pair pass needs the coordinates again, so TV and TV1
-//    are separate (TV1 holds the data until the assembly), and after the elimination the
-//    weight vectors w^ and g (float pairs) take their places.  Gathering the coordinates
-//    a second time instead cost more than the extra warps gained (n = 1M, m = 60: 99.0 ->
-//    102.3 ms; m = 45: 48.2 -> 50.0 ms).
+// The elimination's two column buffers TV and TV1 hold the unscaled entries of columns j
+// and j+1:
+//  - forward kernel (and the gradient kernel where it gathers twice, see
+//    regather_capable): they reuse CX and CY, which are dead after the assembly, and the
+//    data go straight into A's border row, so a block takes two vectors besides A (at
+//    m = 60, 16.6 KB instead of 17.6 KB: thirteen 32-lane blocks fit on an SM instead of
+//    twelve).  The adjoint's weight vectors w^ and g (float pairs) then sit at the start
+//    of A once the backward solves have read the factor;
+//  - gradient kernel otherwise: TV and TV1 are separate (TV1 holds the data until the
+//    assembly), and after the elimination w^ and g take their places.
 struct WarpArea {
   double* A;
   float2 *CX, *CY, *CZ;
   double *TV, *TV1;   // elimination: unscaled entries of columns j and j+1
   float2 *WHf, *GVf;  // gradient, after the elimination: w^ and g as float pairs
-  __host__ __device__ static int doubles(int K, bool grad, bool sphere = false) {
-    const SchedSize S(K);
-    return align_up(S.NT, 2) + ((sphere ? 3 : 2) + (grad ? 2 : 0)) * align_up(K + 1, 2);
+  bool regather;      // gradient: coordinates gathered again after the elimination
+  __host__ __device__ static bool separate(bool grad, int G, bool regather) {
+    return grad && !(regather && regather_capable(grad, G));
   }
-  __device__ WarpArea(double* base, int K, bool grad, bool sphere = false) {
+  __host__ __device__ static int doubles(int K, bool grad, int G, bool sphere = false, bool regather = false) {
+    const SchedSize S(K);
+    const bool sep = separate(grad, G, regather);
+    return align_up(S.NT, 2) + ((sphere ? 3 : 2) + (sep ? 2 : 0)) * align_up(K + 1, 2);
+  }
+  __device__ WarpArea(double* base, int K, bool grad, int G, bool sphere = false, bool regather_ = false) {
     const SchedSize S(K);
     const int V = align_up(K + 1, 2);
+    regather = regather_ && regather_capable(grad, G);
     A = base;
     CX = reinterpret_cast<float2*>(A + align_up(S.NT, 2));
     CY = CX + V;
     CZ = sphere ? CY + V : CY;
-    if (grad) {
+    if (separate(grad, G, regather)) {
       TV = reinterpret_cast<double*>(CY + (sphere ? 2 : 1) * V);
       TV1 = TV + V;
       WHf = reinterpret_cast<float2*>(TV1);
@@ -89,7 +106,8 @@ struct WarpArea {
     } else {
       TV = reinterpret_cast<double*>(CX);
       TV1 = reinterpret_cast<double*>(CY);
-      WHf = GVf = nullptr;
+      WHf = reinterpret_cast<float2*>(A);  // K entries each; 2K <= NT for every K >= 2
+      GVf = WHf + K;
     }
   }
 };
@@ -418,10 +436,12 @@ __device__ __forceinline__ bool process_location(int64_t i, bool active, const F
     js = 0;
   }
   const double2 ps = F.xy[js];
-  // ---- gather: centred, 1/beta-scaled coordinates (as float pairs), and the data: in the
-  // forward kernel straight into the border row K of A (slot tri_off(K, c) + K - c; the
-  // location's own y lands in A[2]), in the gradient kernel into TV1, copied to the border
-  // by the assembly (that order measured 1% faster there)
+  // ---- gather: centred, 1/beta-scaled coordinates (as float pairs), and the data: with
+  // two vectors per block straight into the border row K of A (slot tri_off(K, c) + K - c;
+  // the location's own y lands in A[2]), with separate column buffers into TV1, copied to
+  // the border by the assembly (that order measured 1% faster there)
+  const bool regather = regather_capable(GRAD, G) && W.regather;  // warp-uniform
+  const bool sep_buffers = GRAD && !regather;
 #pragma unroll
   for (int s = 0; s < NSG; ++s) {
     const int p = sub + G * s;
@@ -436,7 +456,7 @@ __device__ __forceinline__ bool process_location(int64_t i, bool active, const F
         coord_offsets<SPHERE>(F, tc, ps, js, j, xv, yv, zv);
         fv = F.yf[j];
       }
-      if constexpr (GRAD) {
+      if (sep_buffers) {
         W.TV1[p] = fv;
       } else {
         A[tri_off(K, p) + K - p] = fv;
@@ -450,7 +470,7 @@ __device__ __forceinline__ bool process_location(int64_t i, bool active, const F
     CX[m] = make_float2(0.0f, 0.0f);
     CY[m] = make_float2(0.0f, 0.0f);
     if constexpr (SPHERE) CZ[m] = make_float2(0.0f, 0.0f);
-    if constexpr (GRAD) {
+    if (sep_buffers) {
       W.TV1[m] = F.yf[js];
     } else {
       A[tri_off(K, m) + K - m] = F.yf[js];
@@ -462,12 +482,12 @@ __device__ __forceinline__ bool process_location(int64_t i, bool active, const F
     bad_idx = (__ballot_sync(0xffffffffu, bad_idx) & gmask) != 0u;
   }
   __syncwarp();
-  // ---- assemble: diagonal (and in the gradient kernel the data border), then the
-  // correlation pairs
+  // ---- assemble: diagonal (and, with separate column buffers, the data border), then
+  // the correlation pairs
   for (int c = sub; c < K; c += G) {
     const int o = tri_off(K, c);
     A[o] = (c >= mi && c < m) ? 1.0 : tc.gamma1;
-    if constexpr (GRAD) A[o + K - c] = W.TV1[c];
+    if (sep_buffers) A[o + K - c] = W.TV1[c];
   }
   if (sub == 0) A[0] = 0.0;
   // Two pairs per lane per iteration so one pair's loads overlap the other's FMAs.
@@ -709,7 +729,29 @@ __device__ __forceinline__ bool process_location(int64_t i, bool active, const F
     __syncwarp();
     return good;
   }
-  // ---- adjoint: w = L_J^{-T} (row m of L), alpha~ = L_J^{-T} (row K of L)
+  // ---- adjoint: with two vectors per block, the coordinates again first (the
+  // elimination used CX and CY as its column buffers; the same values as the first
+  // gather); then w = L_J^{-T} (row m of L) and alpha~ = L_J^{-T} (row K of L)
+  if (regather) {
+#pragma unroll
+    for (int s = 0; s < NSG; ++s) {
+      const int p = sub + G * s;
+      if (p < m) {
+        double xv = 0.0, yv = 0.0, zv = 0.0;
+        if (p < mi) {
+          int j = row[p];
+          if (check && (unsigned long long)(int64_t)j >= (unsigned long long)F.nidx) j = 0;
+          coord_offsets<SPHERE>(F, tc, ps, js, j, xv, yv, zv);
+        }
+        CX[p] = d2f_pair(xv);
+        CY[p] = d2f_pair(yv);
+      }
+    }
+    if (sub == 0) {
+      CX[m] = make_float2(0.0f, 0.0f);
+      CY[m] = make_float2(0.0f, 0.0f);
+    }
+  }
   constexpr int NS = (KCAP - 1 + G - 1) / G;  // slots of the K-1 <= KCAP-1 neighbour entries
   // The two unit backward solves run in double-float arithmetic on the FP32 pipe: each
   // step of their serial chain would otherwise wait behind the other warps' FP64 work.
@@ -757,8 +799,10 @@ __device__ __forceinline__ bool process_location(int64_t i, bool active, const F
   const double rsa = rs * tc.inv_sigma2;  // alpha = alpha~ / sigma2
   // w^ and g are kept as float pairs for the beta pair sums below (double-float products
   // there: the same ~2^-46 relative precision as h(u) itself, and no FP64 instruction).
+  // With two vectors per block they go to the start of A, which no lane reads any more.
   float2* __restrict__ WHf = W.WHf;
   float2* __restrict__ GVf = W.GVf;
+  if (regather) __syncwarp();
   double pT = 0.0;
 #pragma unroll
   for (int t = 0; t < NS; ++t) {

@@ -83,6 +83,7 @@ struct LikArgs {
   int64_t i0 = 0, i1 = 0;            // ordered locations [i0, i1) are evaluated
   int64_t n_index = 0;               // entries of xy / yf (0: n)
   bool check_idx = false;            // check nbr / self entries against [0, n_index)
+  bool regather = false;             // gradient, 8 lanes: two vectors per block (WarpArea)
 };
 
 // Shared-memory layout for block size K (= m + 1), G lanes per location (32/G locations
@@ -90,20 +91,24 @@ struct LikArgs {
 struct SmemLayout {
   SchedSize S;
   int group_doubles, per_warp_doubles;
-  __host__ __device__ SmemLayout(int K, bool grad, int G, bool sphere = false)
+  __host__ __device__ SmemLayout(int K, bool grad, int G, bool sphere = false, bool regather = false)
       : S(K),
-        group_doubles(WarpArea::doubles(K, grad, sphere)),
-        per_warp_doubles((32 / G) * WarpArea::doubles(K, grad, sphere)) {}
+        group_doubles(WarpArea::doubles(K, grad, G, sphere, regather)),
+        per_warp_doubles((32 / G) * WarpArea::doubles(K, grad, G, sphere, regather)) {}
   __host__ __device__ int bytes(int W) const { return S.sched_bytes + S.pairs_bytes + W * per_warp_doubles * 8; }
 };
 
+// Up to 13 warps per CTA for the forward pass (its two-vector blocks fit thirteen on an
+// SM at m = 60) and 12 for the gradient; the 8-lane gradient kernels are bounded for 16
+// warps per SM (two CTAs of 8, at most 128 registers a thread), which their second-gather
+// layout reaches at m = 25.
 template <bool GRAD, int G, bool SPHERE>
-__global__ void __launch_bounds__(GRAD ? 384 : 32 * kMaxCtaWarps) vecchia_lik_kernel(const LikArgs a) {
+__global__ void __launch_bounds__(GRAD ? (G == 8 ? 512 : 384) : 32 * kMaxCtaWarps) vecchia_lik_kernel(const LikArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int NL = 32 / G;
   const int K = a.m + 1;
   constexpr bool sphere = SPHERE;
-  const SmemLayout L(K, GRAD, G, sphere);
+  const SmemLayout L(K, GRAD, G, sphere, a.regather);
   uint16_t* sched = reinterpret_cast<uint16_t*>(smem);
   uint32_t* pairs = reinterpret_cast<uint32_t*>(smem + L.S.sched_bytes);
   const int lane = threadIdx.x & 31;
@@ -111,7 +116,7 @@ __global__ void __launch_bounds__(GRAD ? 384 : 32 * kMaxCtaWarps) vecchia_lik_ke
   const int W = blockDim.x >> 5;
   const int grp = lane / G, sub = lane % G;
   const WarpArea area(reinterpret_cast<double*>(smem + L.S.sched_bytes + L.S.pairs_bytes) +
-                          wib * L.per_warp_doubles + grp * L.group_doubles, K, GRAD, sphere);
+                          wib * L.per_warp_doubles + grp * L.group_doubles, K, GRAD, G, sphere, a.regather);
   build_schedules(K, sched, pairs);
   __syncthreads();
 
@@ -195,6 +200,7 @@ __global__ void __launch_bounds__(128) vecchia_finalize_kernel(const double* __r
 namespace {
 struct LaunchCfg {
   int G = 32, W = 4, blocks = 0, smem = 0;
+  bool regather = false;  // gradient, 8 lanes: coordinates gathered twice, two vectors per block
 };
 
 template <bool GRAD, bool SPHERE>
@@ -250,36 +256,49 @@ void set_tuned(int dev, int K, bool grad, int G, int W) {
 }
 
 // Launch shape for lanes-per-location G: W (forced_W > 0, else the value giving the most
-// resident warps per SM, ties to the larger CTA) and a persistent grid of one wave.
+// resident warps per SM, ties to the larger CTA) and a persistent grid of one wave.  An
+// 8-lane gradient launch gathers the coordinates twice (two vectors per block) when that
+// gives at least 20% more resident warps (regather_capable in block.cuh has the
+// measurements behind the threshold).
 int shape_for(int K, bool grad, int G, int forced_W, LaunchCfg* cfg, bool sphere = false) {
   if (K > max_k_for_lanes(G)) return VECCHIA_EINVAL;  // narrow groups hold small blocks only
   int dev = 0, sms = 0, smem_optin = 0;
   VECCHIA_CUDA_TRY(cudaGetDevice(&dev));
   VECCHIA_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   VECCHIA_CUDA_TRY(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  const SmemLayout L(K, grad, G, sphere);
   void* kern = lik_kernel(grad, G, sphere);
   cudaFuncAttributes fa;
   VECCHIA_CUDA_TRY(cudaFuncGetAttributes(&fa, kern));  // the forward kernel takes up to 13 warps
-  int best_warps = -1;
-  for (int W : {13, 12, 11, 10, 9, 8, 6, 4, 2, 1}) {
-    if (forced_W > 0 && W != forced_W) continue;
-    if (32 * W > fa.maxThreadsPerBlock) continue;
-    const int bytes = L.bytes(W);
-    if (bytes > smem_optin) continue;
-    VECCHIA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-    int per_sm = 0;
-    VECCHIA_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, W * 32, bytes));
-    const int warps = std::min(per_sm * W, 16);
-    if (per_sm > 0 && warps > best_warps) {
-      best_warps = warps;
-      cfg->G = G;
-      cfg->W = W;
-      cfg->blocks = per_sm * sms;
-      cfg->smem = bytes;
+  // most resident warps per SM (capped at 16 by the registers) for one layout, or -1
+  auto best_for = [&](bool regather, LaunchCfg* out) -> int {
+    const SmemLayout L(K, grad, G, sphere, regather);
+    int best_warps = -1;
+    for (int W : {13, 12, 11, 10, 9, 8, 6, 4, 2, 1}) {
+      if (forced_W > 0 && W != forced_W) continue;
+      if (32 * W > fa.maxThreadsPerBlock) continue;
+      const int bytes = L.bytes(W);
+      if (bytes > smem_optin) continue;
+      if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess) return -2;
+      int per_sm = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, W * 32, bytes) != cudaSuccess) return -2;
+      const int warps = std::min(per_sm * W, 16);
+      if (per_sm > 0 && warps > best_warps) {
+        best_warps = warps;
+        out->G = G;
+        out->W = W;
+        out->blocks = per_sm * sms;
+        out->smem = bytes;
+        out->regather = regather;
+      }
     }
-  }
-  if (best_warps <= 0) return VECCHIA_EINVAL;
+    return best_warps;
+  };
+  LaunchCfg sep, rg;
+  const int ws = best_for(false, &sep);
+  const int wr = regather_capable(grad, G) ? best_for(true, &rg) : -1;
+  if (ws == -2 || wr == -2) return VECCHIA_ECUDA;
+  if (ws <= 0 && wr <= 0) return VECCHIA_EINVAL;
+  *cfg = (wr > 0 && 5 * wr >= 6 * ws) ? rg : sep;
   VECCHIA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, cfg->smem));
   return VECCHIA_OK;
 }
@@ -369,6 +388,7 @@ int launch_with(Plan* p, const double* y_dev, const double* theta, bool grad, co
   a.radius = p->radius;
   a.i0 = i0;
   a.i1 = i1;
+  a.regather = cfg.regather;
   launch_lik(cfg, grad, a, stream);
   VECCHIA_CUDA_TRY(cudaGetLastError());
   if (out_dev) {
