@@ -201,6 +201,7 @@ namespace {
 struct LaunchCfg {
   int G = 32, W = 4, blocks = 0, smem = 0;
   bool regather = false;  // gradient, 8 lanes: coordinates gathered twice, two vectors per block
+  int sms = 0;            // SMs of the device
 };
 
 template <bool GRAD, bool SPHERE>
@@ -260,13 +261,55 @@ void set_tuned(int dev, int K, bool grad, int G, int W) {
 // 8-lane gradient launch gathers the coordinates twice (two vectors per block) when that
 // gives at least 20% more resident warps (regather_capable in block.cuh has the
 // measurements behind the threshold).
+//
+// Shapes are cached per (device, K, kind, G, forced W, metric): the occupancy queries
+// behind one cost tens of microseconds of host time.  The dynamic shared-memory limit
+// last set on each kernel is recorded, so that a cached shape sets it again only where a
+// launch of another block size changed it.
+struct ShapeEntry {
+  int dev, K, grad, G, W, sphere;
+  LaunchCfg cfg;
+};
+struct SmemLimit {
+  int dev;
+  void* kern;
+  int bytes;
+};
+std::mutex g_shape_mu;
+std::vector<ShapeEntry> g_shapes;
+std::vector<SmemLimit> g_smem_limits;
+
+// Sets the kernel's dynamic shared-memory limit to `bytes` unless it already is.
+// Called with g_shape_mu held.
+int set_smem_limit(int dev, void* kern, int bytes) {
+  for (SmemLimit& l : g_smem_limits)
+    if (l.dev == dev && l.kern == kern) {
+      if (l.bytes != bytes) {
+        VECCHIA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+        l.bytes = bytes;
+      }
+      return VECCHIA_OK;
+    }
+  VECCHIA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  g_smem_limits.push_back({dev, kern, bytes});
+  return VECCHIA_OK;
+}
+
 int shape_for(int K, bool grad, int G, int forced_W, LaunchCfg* cfg, bool sphere = false) {
   if (K > max_k_for_lanes(G)) return VECCHIA_EINVAL;  // narrow groups hold small blocks only
   int dev = 0, sms = 0, smem_optin = 0;
   VECCHIA_CUDA_TRY(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_shape_mu);
+  void* kern = lik_kernel(grad, G, sphere);
+  for (const ShapeEntry& e : g_shapes)
+    if (e.dev == dev && e.K == K && e.grad == (int)grad && e.G == G && e.W == forced_W && e.sphere == (int)sphere) {
+      const int rc = set_smem_limit(dev, kern, e.cfg.smem);
+      if (rc) return rc;
+      *cfg = e.cfg;
+      return VECCHIA_OK;
+    }
   VECCHIA_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   VECCHIA_CUDA_TRY(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  void* kern = lik_kernel(grad, G, sphere);
   cudaFuncAttributes fa;
   VECCHIA_CUDA_TRY(cudaFuncGetAttributes(&fa, kern));  // the forward kernel takes up to 13 warps
   // most resident warps per SM (capped at 16 by the registers) for one layout, or -1
@@ -287,6 +330,7 @@ int shape_for(int K, bool grad, int G, int forced_W, LaunchCfg* cfg, bool sphere
         out->G = G;
         out->W = W;
         out->blocks = per_sm * sms;
+        out->sms = sms;
         out->smem = bytes;
         out->regather = regather;
       }
@@ -300,6 +344,14 @@ int shape_for(int K, bool grad, int G, int forced_W, LaunchCfg* cfg, bool sphere
   if (ws <= 0 && wr <= 0) return VECCHIA_EINVAL;
   *cfg = (wr > 0 && 5 * wr >= 6 * ws) ? rg : sep;
   VECCHIA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, cfg->smem));
+  bool known = false;  // the search above set other limits on the way
+  for (SmemLimit& l : g_smem_limits)
+    if (l.dev == dev && l.kern == kern) {
+      l.bytes = cfg->smem;
+      known = true;
+    }
+  if (!known) g_smem_limits.push_back({dev, kern, cfg->smem});
+  g_shapes.push_back({dev, K, (int)grad, G, forced_W, (int)sphere, *cfg});
   return VECCHIA_OK;
 }
 
@@ -352,8 +404,27 @@ int lanes_for(int K, bool grad) {
 }
 
 namespace {
-int launch_with(Plan* p, const double* y_dev, const double* theta, bool grad, const LaunchCfg& cfg,
+// The launch for `count` locations: with fewer location groups than the shape's resident
+// warps, the groups are spread over every SM with fewer warps per CTA.  A full-size CTA
+// would put them all on a few SMs, whose FP64 pipes (one warp-instruction per 64 cycles
+// per sub-partition, whatever the active lanes) would then run the whole problem while
+// the rest of the GPU idles: at n = 2,000, m = 10 the kernel took 35 us that way, 26 us
+// spread.  Each warp keeps the same locations (warp w takes group w); only the per-CTA
+// grouping of the warps' sums changes, and with it the last bits of the totals.
+LaunchCfg fit_to_work(LaunchCfg c, int K, bool grad, bool sphere, int64_t count) {
+  const int NL = 32 / c.G;
+  const int64_t groups = (count + NL - 1) / NL;
+  if (c.sms <= 0 || groups >= (int64_t)c.blocks * c.W) return c;
+  const int W = (int)std::max<int64_t>(1, std::min<int64_t>(c.W, (groups + c.sms - 1) / c.sms));
+  c.W = W;
+  c.blocks = (int)((groups + W - 1) / W);
+  c.smem = SmemLayout(K, grad, c.G, sphere, c.regather).bytes(W);
+  return c;
+}
+
+int launch_with(Plan* p, const double* y_dev, const double* theta, bool grad, const LaunchCfg& shape,
                 double* out_dev, double* terms_dev, cudaStream_t stream, int64_t i0, int64_t i1) {
+  const LaunchCfg cfg = fit_to_work(shape, p->m + 1, grad, p->metric == 1, i1 - i0);
   const int64_t nw = (int64_t)cfg.blocks * cfg.W;
   if (p->partial_cap < nw * 4) {
     if (p->d_partial) cudaFree(p->d_partial);
@@ -518,6 +589,7 @@ int predict(Plan* p, const double* xy_new_host, int64_t n_new, const double* y_d
   }
   LaunchCfg cfg;
   if (!rc) rc = pick_config((int)m + 1, false, &cfg, p->metric == 1);
+  if (!rc) cfg = fit_to_work(cfg, (int)m + 1, false, p->metric == 1, n_new);
   const int64_t nw = (int64_t)cfg.blocks * cfg.W;
   if (!rc && p->partial_cap < nw * 4) {
     if (p->d_partial) cudaFree(p->d_partial);
@@ -723,6 +795,7 @@ extern "C" int vecchia_loglik_noalloc(const double* xy_dev, const double* y_dev,
   // it is capped to the warps the scratch can hold.
   const int max_blocks = kNoAllocWarps / cfg.W;
   if (cfg.blocks > max_blocks) cfg.blocks = max_blocks;
+  cfg = fit_to_work(cfg, m + 1, false, false, n);
   rc = launch_matern_table(theta[2], tab, s);
   if (rc) return rc;
   VECCHIA_CUDA_TRY(cudaMemsetAsync(errloc, 0xFF, sizeof(unsigned long long), s));
