@@ -86,7 +86,7 @@ __device__ __forceinline__ void run_item(const FieldDesc& fd, int64_t tile, cons
   const SchedSize S(K);
   const uint16_t* sched = reinterpret_cast<const uint16_t*>(smem + a.sched_off[fd.kidx]);
   const uint32_t* pairs = reinterpret_cast<const uint32_t*>(smem + a.pairs_off[fd.kidx]);
-  const WarpArea area(base + grp * WarpArea::doubles(K, GRAD, G), K, GRAD, G);
+  const WarpArea area(base + grp * group_doubles(K, GRAD, G), K, GRAD, G);
   Accum acc;
   const int64_t i0 = tile * kTile;
   const int64_t i1 = min(fd.n, i0 + kTile);
@@ -307,11 +307,11 @@ int build_batch(const Plan* const* plans, const double* const* ys, int nfields, 
   // largest blocks (which carry most of the flops).
   int full_area = 0;
   for (int f = 0; f < nfields; ++f)
-    if (fd[f].lanes == 32) full_area = std::max(full_area, WarpArea::doubles(fd[f].m + 1, want_grad != 0, 32));
+    if (fd[f].lanes == 32) full_area = std::max(full_area, group_doubles(fd[f].m + 1, want_grad != 0, 32));
   if (full_area > 0) {
     for (int f = 0; f < nfields; ++f) {
       const int K = fd[f].m + 1;
-      while (fd[f].lanes < 32 && (32 / fd[f].lanes) * WarpArea::doubles(K, want_grad != 0, fd[f].lanes) > full_area)
+      while (fd[f].lanes < 32 && (32 / fd[f].lanes) * group_doubles(K, want_grad != 0, fd[f].lanes) > full_area)
         fd[f].lanes *= 2;
     }
   }
@@ -335,7 +335,7 @@ int build_batch(const Plan* const* plans, const double* const* ys, int nfields, 
     off += S.pairs_bytes;
   }
   for (int f = 0; f < nfields; ++f)  // a warp holds 32/lanes blocks of its field's size
-    area = std::max(area, (32 / fd[f].lanes) * WarpArea::doubles(fd[f].m + 1, want_grad != 0, fd[f].lanes));
+    area = std::max(area, (32 / fd[f].lanes) * group_doubles(fd[f].m + 1, want_grad != 0, fd[f].lanes));
   a.area_off = off;
   a.area_doubles = area;
   int rc = want_grad ? batched_config<true>(off, a.area_doubles * 8, &b->W, &b->blocks, &b->smem)

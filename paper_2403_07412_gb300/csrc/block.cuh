@@ -112,6 +112,19 @@ struct WarpArea {
   }
 };
 
+// Stride, in doubles, between the areas of a warp's 32/G location groups: the area
+// (WarpArea::doubles) plus 16 bytes where the groups would otherwise start on the same
+// shared-memory banks.  The groups run one instruction stream, so each access of a warp
+// touches the same slot of every group's area; with 8 lanes and an area that is a
+// multiple of 128 bytes (m = 16, 27, 29, 30 among others) the four groups' 64-bit
+// accesses met on 16 of the 32 banks, four wavefronts where two serve (4 lanes: a
+// multiple of 64 bytes puts eight groups on 16 banks).
+__host__ __device__ inline int group_doubles(int K, bool grad, int G, bool sphere = false, bool regather = false) {
+  const int d = WarpArea::doubles(K, grad, G, sphere, regather);
+  const int bytes = 8 * d;
+  return ((G == 8 && bytes % 128 == 0) || (G == 4 && bytes % 64 == 0)) ? d + 2 : d;
+}
+
 // Element schedules for block size K: sched[e] = (row, col) of packed slot e;
 // pairs[q] = (row, col, slot) of the q-th strictly-lower pair of the K x K block.
 __device__ __forceinline__ void build_schedules(int K, uint16_t* sched, uint32_t* pairs) {

@@ -93,8 +93,8 @@ struct SmemLayout {
   int group_doubles, per_warp_doubles;
   __host__ __device__ SmemLayout(int K, bool grad, int G, bool sphere = false, bool regather = false)
       : S(K),
-        group_doubles(WarpArea::doubles(K, grad, G, sphere, regather)),
-        per_warp_doubles((32 / G) * WarpArea::doubles(K, grad, G, sphere, regather)) {}
+        group_doubles(vecchia::group_doubles(K, grad, G, sphere, regather)),
+        per_warp_doubles((32 / G) * vecchia::group_doubles(K, grad, G, sphere, regather)) {}
   __host__ __device__ int bytes(int W) const { return S.sched_bytes + S.pairs_bytes + W * per_warp_doubles * 8; }
 };
 
