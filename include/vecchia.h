@@ -329,7 +329,11 @@ int vecchia_loglik_noalloc(const double* xy_dev, const double* y_dev, const int3
  * every later call with the same block size and kind (want_grad) on this device,
  * including the batched call's layouts created afterwards.  Without tuning, blocks of
  * up to 16 rows use 4 lanes, up to 32 rows 8, up to 48 rows 16 (forward) or 32
- * (gradient), larger ones a full warp.
+ * (gradient), larger ones a full warp; a call over fewer locations than would give
+ * one group of them per SM sub-partition widens those defaults (up to 16 lanes), and
+ * a call with fewer groups than the shape's resident warps spreads them over every SM
+ * with fewer warps per CTA.  Results are deterministic for a given plan, range and
+ * shape; a different shape changes only the order of the final additions.
  * Not in the paper (its batched kernels are library routines).
  *   y_dev, theta : as for vecchia_loglik (theta on the host).
  *   lanes_out, warps_out : host int32 (may be NULL): the chosen shape.  For m >
