@@ -319,7 +319,7 @@ def run_nu_steps(V, dev, n=100_000, m=30, steps=8):
     y2 = torch.as_tensor(datagen.field_rff(xy2, theta0, seed + 1007, device=dev), device=dev)
     p2 = V.Plan(xy2, m, order=V.ORDER_RANDOM, seed=seed)
     t0 = time.perf_counter()
-    res = mle.fit(p2, y2, (0.8, 0.08, 1.0, 0.02), estimate_nu=True, max_iter=40)
+    res = mle.fit(p2, y2, (0.8, 0.08, 1.0, 0.02), estimate_nu=True)
     fit_s = time.perf_counter() - t0
     p2.close()
     return {"workload": f"{n} uniform locations, m = {m}, Matern, autograd step at a new nu each step",
@@ -327,7 +327,8 @@ def run_nu_steps(V, dev, n=100_000, m=30, steps=8):
             "table_builds_per_step": 2,
             "mle_fit": {"n": n2, "m": m, "evaluations": res.evaluations, "seconds": round(fit_s, 3),
                         "ms_per_evaluation": round(fit_s / max(res.evaluations, 1) * 1e3, 3),
-                        "theta_hat": [round(float(v), 5) for v in res.theta], "converged": res.converged}}
+                        "theta_hat": [round(float(v), 5) for v in res.theta], "theta_true": list(theta0),
+                        "iterations": res.iterations, "converged": res.converged, "message": res.message}}
 
 
 def run_m_sweep(V, dev, peak_tflops, n=250_000, ms=(10, 30, 60, 90, 120, 150)):
